@@ -1,0 +1,430 @@
+#!/usr/bin/env python
+"""PANDA message-passing throughput on one GB300 (and N independent replicas).
+
+One step = one message-passing iteration (Eqs. 2-7: the four Tanimoto
+products, the W, P, C updates, the diagonals and h) of the human-sized
+network: 1000 TFs x 17000 genes, synthetic priors shaped like the paper's
+(motif prior W Bernoulli(0.05), PPI prior P Bernoulli(0.01) with unit
+diagonal, C the Pearson correlation of 200 samples from 20 latent factors),
+alpha = 0.1.  C alone is 1.16 GB, far larger than L2, so no L2 flush is
+needed between iterations.
+
+Prints one JSON line.  ``value`` is iterations/s summed over ranks, timed with
+CUDA events on the library's stream with the inputs already in HBM; ``e2e``
+is the same metric through the C ABI from pinned host buffers, the
+host-to-device copy of the inputs and the read-back of the networks inside
+the timed region.  ``--impl reference`` times the FP64 oracle on the host
+cores on a bounded sample of the same iteration instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1507_07039_gb300 import synth  # noqa: E402
+
+METRIC = "PANDA iterations/s + TFLOP/s, BF16-split vs FP32, at max|ΔW|≤1e-4 vs FP64"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}
+SMS, FP32_LANES = 152, 128
+ALPHA = 0.1
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (N > 1: independent replicas, no data-path collective)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def dist_init(world: int, backend: str = "nccl"):
+    if world > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend)
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of a float over all ranks (the slowest rank sets the job's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id is not None:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_id_for(device_index: int) -> str | None:
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(device_index)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# workload accounting
+# ---------------------------------------------------------------------------
+
+def algorithmic_flops(T: int, G: int) -> float:
+    """Flops one iteration must do: W.C (2TG^2), P.W (2T^2 G), and the symmetric
+    halves of W'^T.W' (TG^2) and W'.W'^T (T^2 G)."""
+    return 3.0 * T * G * G + 3.0 * T * T * G
+
+
+def kernel_algorithmic_work(name: str, T: int, G: int) -> tuple[float, str]:
+    """Algorithmic flops one launch of a kernel does, and the unit."""
+    if name in ("k_phase1",):            # W . C_off product + fused update
+        return 2.0 * T * G * G, "flop"
+    if name in ("k_rn",):
+        return 2.0 * T * T * G, "flop"
+    if name in ("k_phase2",):            # symmetric halves of both similarity products
+        return 1.0 * T * G * G + 1.0 * T * T * G, "flop"
+    if name in ("k_tc_phase1",):         # both products of phase 1 in one launch
+        return 2.0 * T * G * G + 2.0 * T * T * G, "flop"
+    if name in ("k_tc_phase2",):
+        return 1.0 * T * G * G + 1.0 * T * T * G, "flop"
+    return 0.0, "flop"
+
+
+def load_peaks() -> tuple[dict, str]:
+    try:
+        return json.load(open(PEAKS_FILE)), "measured"
+    except (OSError, ValueError):
+        return dict(FALLBACK), "fallback"
+
+
+def traffic_for(kernel: str, workload: str) -> float | None:
+    """DRAM bytes per launch from a committed ncu capture, if the kernel's
+    source is unchanged since it was taken."""
+    try:
+        rec = json.load(open(TRAFFIC_FILE))[f"{kernel}@{workload}"]
+    except (OSError, ValueError, KeyError):
+        return None
+    src = os.path.join(ROOT, "paper_1507_07039_gb300", "csrc", rec["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return float(rec["bytes_per_launch"]) if sha == rec["source_sha"] else None
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on a bounded sample of one iteration
+# ---------------------------------------------------------------------------
+
+class OracleSample:
+    """Times the oracle on a fraction f of one iteration of the workload: f*T
+    rows of W' (Eqs. 2-4), f*T rows of P' and f*G rows of C' (Eq. 5; their
+    inputs are the current W standing in for W', the same operation count).
+    The diagonals and h (Eqs. 6-7) are O(T^2 + G^2 + TG) and not sampled.
+    Seconds per iteration = sampled seconds / f."""
+
+    def __init__(self, W0, P0, C0, threads: int):
+        from oracle.oracle import Oracle
+        self.orc = Oracle()
+        self.orc.set_threads(threads)
+        self.threads = threads
+        self.W, self.P, self.C = self.orc.normalize(W0, P0, C0)
+        self.T, self.G = self.W.shape
+        self.cursor = 0
+
+    def run(self, frac: float) -> float:
+        """Seconds per full iteration estimated from one sample of size frac."""
+        rT, rG = max(1, round(frac * self.T)), max(1, round(frac * self.G))
+        rows_t = (self.cursor + np.arange(rT)) % self.T
+        rows_g = (self.cursor + np.arange(rG)) % self.G
+        self.cursor += rT
+        a = ALPHA
+        t0 = time.perf_counter()
+        self.orc.w_rows(self.W, self.P, self.C, a, rows_t)
+        t1 = time.perf_counter()
+        self.orc.p_rows(self.W, self.P, a, rows_t)
+        t2 = time.perf_counter()
+        self.orc.c_rows(self.W, self.C, a, rows_g)
+        t3 = time.perf_counter()
+        return (t1 - t0) / (rT / self.T) + (t2 - t1) / (rT / self.T) + (t3 - t2) / (rG / self.G)
+
+
+def cpu_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+# the two arms
+# ---------------------------------------------------------------------------
+
+def run_reference(args, wl, rank, world):
+    if rank != 0:
+        return
+    W0, P0, C0 = synth.make_inputs(wl)
+    threads = cpu_threads()
+    s = OracleSample(W0, P0, C0, threads)
+    frac = args.ref_frac
+    for _ in range(args.warmup):
+        s.run(frac)
+    t0 = time.perf_counter()
+    est = [s.run(frac) for _ in range(args.steps)]
+    wall = time.perf_counter() - t0
+    sec_per_iter = float(np.median(est))
+    value = 1.0 / sec_per_iter
+    sample = (f"each step: {max(1, round(frac * wl.T))} rows of W', {max(1, round(frac * wl.T))} rows "
+              f"of P', {max(1, round(frac * wl.G))} rows of C' (fraction {frac} of one iteration), "
+              f"scaled to a full iteration")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "T": wl.T, "G": wl.G, "alpha": ALPHA,
+                   "step": "sampled fraction of one message-passing iteration", "parallelism": "none"},
+        "cpu_baseline": {"value": value, "unit": "iterations/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def time_gpu(panda, torch, W0, P0, C0, prec, steps, warmup, world, local_rank, with_clocks):
+    """Device-timed iterations/s of one context (inputs resident in HBM)."""
+    ctx = panda.PandaContext(W0, P0, C0, prec=prec)
+    ctx.run(ALPHA, 0.0, warmup)
+    panda.panda_set_profiling(ctx.h, True)
+    ctx.run(ALPHA, 0.0, 1)  # capture the graphs (one per W buffer parity) outside the timed region
+    ctx.run(ALPHA, 0.0, 1)
+    panda.panda_set_profiling(ctx.h, True)
+    stream = torch.cuda.ExternalStream(ctx.stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(gpu_id_for(local_rank)) if with_clocks else None
+    barrier(world)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+        time.sleep(0.6)  # let the sampler take its first reading
+    e0.record(stream)
+    conv, n, h = ctx.run(ALPHA, 0.0, steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    ck = clocks.stop() if clocks else None
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    kstats = [panda.panda_kernel_stats(ctx.h, i) for i in range(panda.panda_kernel_count(ctx.h))]
+    ctx.close()
+    assert n == steps, (n, steps)
+    return ms, kstats, ck
+
+
+def time_e2e(panda, torch, W0, P0, C0, prec, steps):
+    """Through the C ABI from pinned host buffers: create (H2D + normalise),
+    steps iterations, read back W, P, C (D2H)."""
+    T, G = W0.shape
+    pin = [torch.empty(x.shape, dtype=torch.float32, pin_memory=True).numpy() for x in (W0, P0, C0)]
+    for dst, src in zip(pin, (W0, P0, C0)):
+        np.copyto(dst, src)
+    outs = [torch.empty(x.shape, dtype=torch.float32, pin_memory=True).numpy() for x in (W0, P0, C0)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = panda.PandaContext(*pin, prec=prec)
+    ctx.run(ALPHA, 0.0, steps)
+    panda.panda_get_into(ctx.h, *outs)
+    t1 = time.perf_counter()
+    ctx.close()
+    return t1 - t0, sum(x.nbytes for x in pin) / steps, sum(x.nbytes for x in outs) / steps
+
+
+def run_ours(args, wl, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist_init(world)
+    from paper_1507_07039_gb300 import panda
+    prec = {"fp32": panda.PANDA_FP32, "bf16x3": panda.PANDA_BF16X3}[args.prec]
+    W0, P0, C0 = synth.make_inputs(wl)
+    T, G = wl.T, wl.G
+
+    ms, kstats, ck = time_gpu(panda, torch, W0, P0, C0, prec, args.steps, args.warmup, world,
+                              local_rank, rank == 0)
+    ms_max = max_over_ranks(ms, world, torch.device("cuda", local_rank))
+    value = world * args.steps / (ms_max / 1000.0)
+
+    # the other precision on the same GPU, for the BF16-split vs FP32 comparison
+    other = None
+    if args.compare and prec != panda.PANDA_FP32:
+        ms32, _, _ = time_gpu(panda, torch, W0, P0, C0, panda.PANDA_FP32, max(5, args.steps // 4),
+                              args.warmup, world, local_rank, False)
+        other = {"fp32_iters_per_s": world * max(5, args.steps // 4) / (max_over_ranks(ms32, world, torch.device("cuda", local_rank)) / 1000.0)}
+
+    # dominant kernel and its roofline
+    peaks, peak_src = load_peaks()
+    tot = sum(k[1] for k in kstats) or 1.0
+    kernels = {k[0]: {"launches": k[2], "ms_total": round(k[1], 4),
+                      "ms_avg": round(k[1] / k[2], 5) if k[2] else None, "share": round(k[1] / tot, 4)}
+               for k in kstats}
+    top = max(kstats, key=lambda k: k[1])
+    work, _ = kernel_algorithmic_work(top[0], T, G)
+    avg_s = top[1] / top[2] / 1000.0
+    if prec == panda.PANDA_FP32:
+        peak = SMS * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_src} max clock)"}
+    else:
+        peak = peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+        roof = {"bound": "tensor", "achieved": work / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": f"bf16 dense sustained ({peak_src})",
+                "issued_tensor_tflops": 3.0 * work / avg_s / 1e12}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = top[0]
+    roof["traffic"] = traffic_for(top[0], wl.name)
+
+    e2e = None
+    if args.e2e:
+        sec, bi, bo = time_e2e(panda, torch, W0, P0, C0, prec, args.steps)
+        sec = max_over_ranks(sec, world, torch.device("cuda", local_rank))
+        e2e = {"value": world * args.steps / sec,
+               "unit": "iterations/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+               "note": "create from pinned host buffers (H2D + validation + Z-score), the iterations, "
+                       "read-back of W, P, C (D2H); per-step bytes = totals / steps"}
+
+    cpu = None
+    if rank == 0 and args.cpu_baseline:
+        threads = cpu_threads()
+        s = OracleSample(W0, P0, C0, threads)
+        t0 = time.perf_counter()
+        spi = s.run(args.cpu_frac)
+        el = time.perf_counter() - t0
+        cpu = {"value": 1.0 / spi, "unit": "iterations/s", "cores": threads, "kind": "oracle",
+               "sample": f"fraction {args.cpu_frac} of one iteration ({max(1, round(args.cpu_frac * T))} rows "
+                         f"of W' and of P', {max(1, round(args.cpu_frac * G))} rows of C'), "
+                         f"{el:.1f} s of CPU time, scaled to a full iteration"}
+
+    launches = int(sum(k[2] for k in kstats))
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iterations/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {panda.PANDA_FP32: "f32", panda.PANDA_BF16X3: "bf16x3"}[prec],
+            "data": "synthetic",
+            "config": {"workload": wl.name, "T": T, "G": G, "alpha": ALPHA,
+                       "precision": args.prec, "step": "one message-passing iteration (Eqs. 2-7)",
+                       "l2": "no flush: inputs larger than L2 (C alone is %.2f GB)" % (4.0 * G * G / 1e9),
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "useful_tflops": value / world * algorithmic_flops(T, G) / 1e12,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": ck,
+            "kernels": kernels,
+        }
+        if other:
+            line.update(other)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["fp32", "bf16x3"], default=None)
+    ap.add_argument("--workload", default="human1000x17000")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-compare", dest="compare", action="store_false")
+    ap.add_argument("--cpu-frac", type=float, default=0.1)
+    ap.add_argument("--ref-frac", type=float, default=0.005)
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    rank, world, local_rank = dist_env()
+    wl = synth.get(args.workload)
+    if args.impl == "reference":
+        run_reference(args, wl, rank, world)
+        return
+    if args.prec is None:
+        from paper_1507_07039_gb300 import panda
+        args.prec = "bf16x3" if panda.tensor_path_available() else "fp32"
+    run_ours(args, wl, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * libpanda_gb300: the PANDA message-passing iteration on one NVIDIA GB300.
+ *
+ * PANDA (Glass, Quackenbush, Kepner; "High Performance Computing of Gene
+ * Regulatory Networks using a Message-Passing Model", Section II) iterates
+ * three networks:
+ *   W  T x G  regulatory network, TFs (effector nodes, N_e = T) to genes
+ *             (affected nodes, N_a = G); not symmetric.
+ *   P  T x T  cooperativity network between TFs; symmetric.
+ *   C  G x G  co-regulatory network between genes; symmetric.
+ * Each iteration t = 1, 2, ... computes
+ *   R_ij = Tan(P_i., W_.j)                      (Eq. 3, responsibility)
+ *   A_ij = Tan(W_i., C_.j)                      (Eq. 4, availability)
+ *   W'   = (1-a) W + a/2 (R + A)                 (Eq. 2)
+ *   h    = mean |W' - W|                         (Eq. 7)
+ *   P'_im = (1-a) P_im + a Tan(W'_i., W'_m.)  for i != m          (Eq. 5)
+ *   C'_kj = (1-a) C_kj + a Tan(W'_.k, W'_.j)  for k != j          (Eq. 5)
+ *   P'_ii, C'_jj from the std of the off-diagonal entries of their row (Eq. 6)
+ * with Tan(x, y) = x.y / sqrt(|x|^2 + |y|^2 - |x.y|) (Eq. 1), and stops when
+ * h < tol (Section II-B, tested after the whole iteration).  Before the first
+ * iteration each network is Z-scored (Section II-A, NormalizeNetwork).
+ *
+ * All matrices crossing this interface are dense, row-major, FP32, with no
+ * padding: W has T*G entries, P has T*T, C has G*G (P and C include their
+ * diagonals).  Host pointers are plain host memory (pageable or pinned);
+ * device pointers are CUDA device memory of the current device.
+ *
+ * Return codes: 0 success; 1 PANDA_NOT_CONVERGED (max_iter reached, outputs
+ * valid); negative values are errors and leave a message readable with
+ * panda_last_error().  A context is used by one host thread at a time.
+ */
+#ifndef PANDA_GB300_H
+#define PANDA_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PANDA_OK 0
+#define PANDA_NOT_CONVERGED 1
+#define PANDA_EINVAL (-1)      /* bad argument: NULL, shape <= 0, alpha outside [0,1], tol < 0 */
+#define PANDA_ENOMEM (-2)      /* device allocation failed (or the PANDA_ALLOC_LIMIT_BYTES cap) */
+#define PANDA_ECUDA (-3)       /* a CUDA runtime or driver call failed */
+#define PANDA_ENONFINITE (-4)  /* a non-finite input, or the state became non-finite */
+#define PANDA_EASYM (-5)       /* P0 or C0 is not exactly symmetric */
+#define PANDA_EDEGENERATE (-6) /* a network has zero standard deviation: Z-score undefined */
+#define PANDA_ETIMEOUT (-7)    /* a bounded device-side wait expired */
+#define PANDA_EUNSUPPORTED (-8)/* option not available in this build or on this device */
+
+/* Arithmetic of the four products (the epilogues are FP32 in every mode). */
+typedef enum {
+    PANDA_FP32 = 0,   /* FP32 FFMA products (SIMT) */
+    PANDA_BF16X3 = 1, /* tensor cores: x = hi + lo in BF16, hi*hi + hi*lo + lo*hi, FP32 accumulation */
+    PANDA_BF16X2 = 2, /* reserved: not built */
+    PANDA_FP8MIX = 3  /* reserved: not built */
+} panda_prec;
+
+/* Reading of Eq. 6 (the paper prints no alpha on the diagonal increment). */
+typedef enum {
+    PANDA_DIAG_D1 = 0,         /* X_ii <- (1-a) X_ii + a N sigma_i e^{2 a t}  (default) */
+    PANDA_DIAG_D0_LITERAL = 1, /* X_ii <- (1-a) X_ii +   N sigma_i e^{2 a t}  (as printed) */
+    PANDA_DIAG_D2_SIM = 2      /* as D1, sigma over row i of the new similarity matrix */
+} panda_diag;                  /* N = G (N_a) for P and T (N_e) for C, as Eq. 6 pairs them */
+
+typedef struct {
+    int prec;          /* panda_prec, default PANDA_FP32 */
+    int diag;          /* panda_diag, default PANDA_DIAG_D1 */
+    int normalize;     /* 1 (default): Z-score W0, P0, C0 at create; 0: use them as given */
+    int t0;            /* iterations already done; the next iteration uses t = t0 + 1 (default 0) */
+    int graph_iters;   /* iterations captured per CUDA-graph launch in panda_run (default 8; 0 = no graph) */
+} panda_opts;
+
+typedef struct panda_ctx panda_ctx;
+
+/* 1 when precision mode prec (panda_prec) is built and runs on the current
+ * device, else 0. */
+int panda_precision_supported(int prec);
+
+/* Fill *o with the defaults listed above. */
+void panda_default_opts(panda_opts *o);
+
+/* Create a context from host inputs (Section II-A: the three seed networks).
+ * W0 is T x G, P0 is T x T, C0 is G x G, row-major FP32 host memory; they are
+ * copied and not retained.  P0 and C0 must be exactly symmetric (PANDA_EASYM)
+ * and every entry finite (PANDA_ENONFINITE).  With opts->normalize each
+ * network is Z-scored with one global mean and population standard deviation
+ * computed in FP64 (PANDA_EDEGENERATE when that deviation is 0).  o may be
+ * NULL for the defaults.  The library owns all device state; it runs on the
+ * current CUDA device and on its own non-blocking stream.  On error *out is
+ * set to NULL and nothing is leaked. */
+int panda_create(panda_ctx **out, int T, int G, const float *W0, const float *P0,
+                 const float *C0, const panda_opts *o);
+
+/* As panda_create, but W0, P0 and C0 are device pointers (not retained, not
+ * freed) and every operation of the context runs on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  The inputs must stay valid until this
+ * call returns. */
+int panda_create_device(panda_ctx **out, int T, int G, const float *dW0, const float *dP0,
+                        const float *dC0, const panda_opts *o, void *stream);
+
+/* One message-passing iteration (Eqs. 2-7) with damping alpha in [0, 1].
+ * *h_out (may be NULL) receives h of Eq. 7 in FP64.  Blocks until done. */
+int panda_step(panda_ctx *ctx, float alpha, double *h_out);
+
+/* Iterate until h < tol (strict, after a whole iteration) or max_iter
+ * iterations (max_iter >= 0).  *iters_out (may be NULL) receives the number of
+ * iterations run by this call, *h_last (may be NULL) the last h.  Returns 0
+ * when converged, PANDA_NOT_CONVERGED when max_iter was reached first.
+ * Blocks until done. */
+int panda_run(panda_ctx *ctx, float alpha, double tol, int max_iter, int *iters_out,
+              double *h_last);
+
+/* Copy the current networks, diagonals included, into caller-allocated host
+ * buffers (T*G, T*T and G*G floats, row-major); any pointer may be NULL to
+ * skip that network. */
+int panda_get(panda_ctx *ctx, float *W, float *P, float *C);
+
+/* As panda_get, into device buffers; ordered on the context's stream and
+ * complete when the call returns. */
+int panda_get_device(panda_ctx *ctx, float *dW, float *dP, float *dC);
+
+/* Networks plus the number of iterations done so far (*t, may be NULL).
+ * panda_set_state replaces the networks (taken as already normalised; P and
+ * C must be exactly symmetric and finite) and the counter; the derived
+ * vectors (row and column norms, FP64 diagonals) are recomputed from them, so
+ * a run continued from panda_set_state matches an uninterrupted one to FP32
+ * rounding.  For a bit-exact resume use panda_save / panda_load. */
+int panda_get_state(panda_ctx *ctx, float *W, float *P, float *C, int *t);
+int panda_set_state(panda_ctx *ctx, const float *W, const float *P, const float *C, int t);
+
+/* Checkpoint and resume.  panda_checkpoint_bytes gives the size of a
+ * checkpoint of ctx; panda_save writes the whole iteration state (networks,
+ * FP64 diagonals, norm vectors, counters, h history) into a caller-allocated
+ * host buffer of that size; panda_load restores it into a context of the
+ * same shape and mode, after which the run continues bit-for-bit as if it
+ * had never stopped. */
+long long panda_checkpoint_bytes(const panda_ctx *ctx);
+int panda_save(panda_ctx *ctx, void *buf, long long bytes);
+int panda_load(panda_ctx *ctx, const void *buf, long long bytes);
+
+/* h of every iteration done so far (oldest first) into h[0..cap); *n receives
+ * the number of iterations recorded (which may exceed cap). */
+int panda_get_history(panda_ctx *ctx, double *h, int cap, int *n);
+
+/* Shape, mode and counters of a context. */
+int panda_info(const panda_ctx *ctx, int *T, int *G, int *prec, int *t);
+
+/* Bytes of device memory the context holds. */
+long long panda_device_bytes(const panda_ctx *ctx);
+
+/* Measurement support (the paper has no counterpart: it times the whole loop
+ * only).  panda_set_profiling(ctx, 1) makes every later iteration record a
+ * CUDA event before and after each of its kernels on the context's stream and
+ * resets the per-kernel accumulators; panda_kernel_count gives the number of
+ * kernels one iteration launches and panda_kernel_stats, for kernel i, its
+ * name (NUL-terminated, truncated to name_cap), the summed device time in ms
+ * and the number of launches that did work since profiling was switched on. */
+int panda_set_profiling(panda_ctx *ctx, int on);
+int panda_kernel_count(const panda_ctx *ctx);
+int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, double *total_ms,
+                       long long *launches);
+
+/* The context's stream as a cudaStream_t. */
+void *panda_stream(const panda_ctx *ctx);
+
+/* Message of the last error on ctx (or of the last failed create when ctx is
+ * NULL); never NULL. */
+const char *panda_last_error(const panda_ctx *ctx);
+
+/* Free everything the context owns.  NULL is ignored. */
+void panda_destroy(panda_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

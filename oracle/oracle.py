@@ -65,6 +65,8 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "oracle_w_row": (None, [i, i, pd, pd, pd, d, i, pd]),
         "oracle_w_col": (None, [i, i, pd, pd, pd, d, i, pd]),
         "oracle_w_rows": (i, [i, i, pd, pd, pd, d, i, pi, pd]),
+        "oracle_eq5_entry": (d, [d, d, pd, l, pd, l, l]),
+        "oracle_diag_value": (d, [pd, i, i, d, d, d, i, i]),
         "oracle_p_rows": (i, [i, i, pd, pd, d, i, pi, pd, pd]),
         "oracle_c_rows": (i, [i, i, pd, pd, d, i, pi, pd, pd]),
         "oracle_step": (i, [i, i, pd, pd, pd, d, i, i, pd, pd, pd, pd]),
@@ -167,6 +169,17 @@ class Oracle:
         if rc:
             raise ValueError(f"oracle_w_rows failed ({rc})")
         return out
+
+    def eq5_entry(self, old, alpha, x, y) -> float:
+        """Eq. 5 for one off-diagonal entry."""
+        x, y = _f64(x), _f64(y)
+        return float(self.lib.oracle_eq5_entry(float(old), float(alpha), _p(x), 1, _p(y), 1, x.size))
+
+    def diag_value(self, row, i, mult, old, alpha, t, diag=DIAG_D1) -> float:
+        """Eq. 6 for one diagonal entry from row i of the updated network."""
+        row = _f64(row)
+        return float(self.lib.oracle_diag_value(_p(row), row.size, int(i), float(mult), float(old),
+                                                float(alpha), int(t), int(diag)))
 
     def p_rows(self, Wn, P, alpha, rows, want_sim=False):
         Wn, P = _f64(Wn), _f64(P)

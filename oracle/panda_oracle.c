@@ -196,6 +196,13 @@ void oracle_w_col(int T, int G, const double *W, const double *P, const double *
 
 /* ---- Eq. 5: off-diagonal P and C from the new W ------------------------- */
 
+double oracle_eq5_entry(double old, double alpha, const double *x, long incx, const double *y,
+                        long incy, long n)
+{
+    double s = oracle_tanimoto(x, incx, y, incy, n);
+    return (1.0 - alpha) * old + alpha * s;
+}
+
 /* Row i of P' (Eq. 5, first line) for each listed i: entries m != i get
  * (1-a) P_im + a Tan(W'_i., W'_m.); the diagonal entry is copied unchanged
  * (Eq. 6 updates it afterwards).  sim (may be NULL) receives the bare
@@ -211,8 +218,9 @@ int oracle_p_rows(int T, int G, const double *Wn, const double *P, double alpha,
         for (int m = 0; m < T; ++m) {
             double s = 0.0, v = P[i * T + m];
             if (m != i) {
-                s = oracle_tanimoto(Wn + i * G, 1, Wn + (long)m * G, 1, G);
-                v = (1.0 - alpha) * P[i * T + m] + alpha * s;
+                v = oracle_eq5_entry(P[i * T + m], alpha, Wn + i * G, 1, Wn + (long)m * G, 1, G);
+                if (sim)
+                    s = oracle_tanimoto(Wn + i * G, 1, Wn + (long)m * G, 1, G);
             }
             out[(long)q * T + m] = v;
             if (sim)
@@ -238,8 +246,9 @@ int oracle_c_rows(int T, int G, const double *Wn, const double *C, double alpha,
         for (int j = 0; j < G; ++j) {
             double s = 0.0, v = C[k * G + j];
             if (j != k) {
-                s = oracle_tanimoto(Wnt + k * T, 1, Wnt + (long)j * T, 1, T);
-                v = (1.0 - alpha) * C[k * G + j] + alpha * s;
+                v = oracle_eq5_entry(C[k * G + j], alpha, Wnt + k * T, 1, Wnt + (long)j * T, 1, T);
+                if (sim)
+                    s = oracle_tanimoto(Wnt + k * T, 1, Wnt + (long)j * T, 1, T);
             }
             out[(long)q * G + j] = v;
             if (sim)
@@ -272,18 +281,24 @@ static double offdiag_row_std(const double *X, int n, int i)
     return sqrt(ss / (double)(n - 1));
 }
 
+double oracle_diag_value(const double *row, int n, int i, double mult, double old, double alpha,
+                         int t, int rule)
+{
+    double growth = exp(2.0 * alpha * (double)t);
+    double gain = (rule == ORACLE_DIAG_D0) ? 1.0 : alpha;
+    double sigma = offdiag_row_std(row - (long)i * n, n, i);
+    return (1.0 - alpha) * old + gain * mult * sigma * growth;
+}
+
 /* Xn holds the updated off-diagonal entries; its diagonal is overwritten with
  * Eq. 6.  mult is N_a (= G) for P and N_e (= T) for C. */
 static void diag_update(int n, double mult, double *Xn, const double *Xold, const double *sim,
                         double alpha, int t, int rule)
 {
-    double growth = exp(2.0 * alpha * (double)t);
-    double gain = (rule == ORACLE_DIAG_D0) ? 1.0 : alpha;
     const double *src = (rule == ORACLE_DIAG_D2) ? sim : Xn;
-    for (int i = 0; i < n; ++i) {
-        double sigma = offdiag_row_std(src, n, i);
-        Xn[(long)i * n + i] = (1.0 - alpha) * Xold[(long)i * n + i] + gain * mult * sigma * growth;
-    }
+    for (int i = 0; i < n; ++i)
+        Xn[(long)i * n + i] = oracle_diag_value(src + (long)i * n, n, i, mult, Xold[(long)i * n + i],
+                                                alpha, t, rule);
 }
 
 /* ---- one iteration -------------------------------------------------------- */

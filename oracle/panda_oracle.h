@@ -69,6 +69,16 @@ void oracle_w_col(int T, int G, const double *W, const double *P, const double *
 int oracle_w_rows(int T, int G, const double *W, const double *P, const double *C,
                   double alpha, int n, const int *rows, double *out);
 
+/* Eq. 5 for one off-diagonal entry: (1 - alpha) old + alpha Tan(x, y). */
+double oracle_eq5_entry(double old, double alpha, const double *x, long incx, const double *y,
+                        long incy, long n);
+
+/* Eq. 6 for one diagonal entry: row holds row i of the updated n x n network
+ * (or of the new similarity matrix under rule D2; its diagonal entry is not
+ * read); mult is N_a (= G) for P and N_e (= T) for C; old is X_ii^(t-1). */
+double oracle_diag_value(const double *row, int n, int i, double mult, double old, double alpha,
+                         int t, int rule);
+
 /* The listed rows of P' (n x T) and C' (n x G) after the off-diagonal update of
  * Eq. 5 from the new W' (Wn); diagonal entries are copied unchanged.  sim (may
  * be NULL) receives the bare similarities, 0 on the diagonal. */

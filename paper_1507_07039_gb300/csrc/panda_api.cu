@@ -1,0 +1,802 @@
+// The C ABI of libpanda_gb300 (declared in include/panda.h): context
+// creation with validation and Z-score normalisation (Section II-A), the
+// iteration driver with its stop test (Section II-B), state access,
+// checkpointing, and the device memory plan.
+#include "panda.h"
+#include "panda_internal.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace panda;
+
+struct panda_ctx {
+    int T = 0, G = 0, Tp = 0, Gp = 0, nbT = 0, nbG = 0;
+    int prec = PANDA_FP32, diag = PANDA_DIAG_D1, normalize = 1, graph_iters = 8;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int cur = 0;  // which W buffer holds the current network
+    Dev d{};
+    Ctl *h_ctl = nullptr;  // pinned mirror of the device control block
+    std::vector<void *> allocs;
+    long long bytes = 0;
+    long long limit = -1;
+    float e2_alpha = -1.0f;  // alpha for which d.e2tab is filled
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int *d_flags = nullptr;
+    double *d_stats = nullptr, *d_partials = nullptr;
+    // per-kernel timing (panda_set_profiling)
+    bool prof = false;
+    std::vector<cudaEvent_t> ev;  // graph_iters (or 1) x (kernels + 1)
+    double k_ms[16] = {};
+    long long k_launches[16] = {};
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct Fail {
+    int code;
+};
+
+int set_err(panda_ctx *c, int code, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_create_error = msg;
+    return code;
+}
+
+#define CU(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return set_err(c, e_ == cudaErrorMemoryAllocation ? PANDA_ENOMEM : PANDA_ECUDA,  \
+                           std::string(#call) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+long long alloc_limit_from_env()
+{
+    const char *s = std::getenv("PANDA_ALLOC_LIMIT_BYTES");
+    if (!s || !*s)
+        return -1;
+    return std::atoll(s);
+}
+
+template <typename T>
+int dalloc(panda_ctx *c, T **p, size_t count)
+{
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0)
+        bytes = 16;
+    if (c->limit >= 0 && c->bytes + (long long)bytes > c->limit) {
+        *p = nullptr;
+        return set_err(c, PANDA_ENOMEM, "device memory plan exceeds PANDA_ALLOC_LIMIT_BYTES");
+    }
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_err(c, PANDA_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    c->allocs.push_back(q);
+    c->bytes += (long long)bytes;
+    e = cudaMemsetAsync(q, 0, bytes, c->stream);
+    if (e != cudaSuccess)
+        return set_err(c, PANDA_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+    *p = static_cast<T *>(q);
+    return 0;
+}
+
+#define DALLOC(ptr, n)                     \
+    do {                                   \
+        int r_ = dalloc(c, &(ptr), (n));   \
+        if (r_)                            \
+            return r_;                     \
+    } while (0)
+
+int plan_memory(panda_ctx *c)
+{
+    Dev &d = c->d;
+    const size_t Tp = c->Tp, Gp = c->Gp;
+    d.T = c->T; d.G = c->G; d.Tp = c->Tp; d.Gp = c->Gp; d.nbT = c->nbT; d.nbG = c->nbG;
+    d.diag = c->diag;
+    for (int b = 0; b < 2; ++b) {
+        DALLOC(d.W[b], Tp * Gp);
+        DALLOC(d.Wt[b], Gp * Tp);
+    }
+    DALLOC(d.Poff, Tp * Tp);
+    DALLOC(d.Coff, Gp * Gp);
+    DALLOC(d.pd, Tp);
+    DALLOC(d.cd, Gp);
+    DALLOC(d.pdf, Tp);
+    DALLOC(d.cdf, Gp);
+    DALLOC(d.rsqP, Tp);
+    DALLOC(d.csqC, Gp);
+    DALLOC(d.rsqW, Tp);
+    DALLOC(d.csqW, Gp);
+    if (c->prec == PANDA_FP32)
+        DALLOC(d.Rn, Tp * Gp);
+    DALLOC(d.wrow_part, (size_t)c->nbG * Tp);
+    DALLOC(d.wcol_part, (size_t)c->nbT * Gp);
+    DALLOC(d.hpart, (size_t)c->nbT * c->nbG);
+    DALLOC(d.ps_sum, (size_t)c->nbT * Tp);
+    DALLOC(d.ps_sq, (size_t)c->nbT * Tp);
+    DALLOC(d.ps_vsq, (size_t)c->nbT * Tp);
+    DALLOC(d.cs_sum, (size_t)c->nbG * Gp);
+    DALLOC(d.cs_sq, (size_t)c->nbG * Gp);
+    DALLOC(d.cs_vsq, (size_t)c->nbG * Gp);
+    DALLOC(d.ctl, 1);
+    DALLOC(d.hist, HIST_CAP);
+    DALLOC(d.e2tab, HIST_CAP + 1);
+    DALLOC(c->d_flags, 4);
+    DALLOC(c->d_stats, 4);
+    DALLOC(c->d_partials, 1024);
+    if (c->prec == PANDA_BF16X3) {
+        for (int b = 0; b < 2; ++b) {
+            DALLOC(d.Wh[b], Tp * Gp);
+            DALLOC(d.Wl[b], Tp * Gp);
+            DALLOC(d.Wth[b], Gp * Tp);
+            DALLOC(d.Wtl[b], Gp * Tp);
+        }
+        DALLOC(d.Ph, Tp * Tp);
+        DALLOC(d.Pl, Tp * Tp);
+        DALLOC(d.Ch, Gp * Gp);
+        DALLOC(d.Cl, Gp * Gp);
+        d.tc_ksplit = 1;
+        int ks = c->nbT * (c->nbT + 1) / 2 < 128 ? 8 : 1;
+        while (ks > 1 && (c->Gp / 128) % ks)  // split K (= Gp) into equal multiples of 128
+            ks >>= 1;
+        d.tc_ksplit = ks;
+        if (ks > 1)
+            DALLOC(d.pacc, (size_t)ks * Tp * Tp);
+    }
+    return 0;
+}
+
+int sync_ctl(panda_ctx *c)
+{
+    CU(cudaMemcpyAsync(c->h_ctl, c->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return 0;
+}
+
+int push_ctl(panda_ctx *c)
+{
+    CU(cudaMemcpyAsync(c->d.ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
+    return 0;
+}
+
+// Copy a rows x cols row-major matrix (host or device) into a padded buffer.
+int upload(panda_ctx *c, float *dst, int ld, const float *src, int rows, int cols)
+{
+    CU(cudaMemcpy2DAsync(dst, (size_t)ld * sizeof(float), src, (size_t)cols * sizeof(float),
+                         (size_t)cols * sizeof(float), rows, cudaMemcpyDefault, c->stream));
+    return 0;
+}
+
+int download(panda_ctx *c, float *dst, const float *src, int ld, int rows, int cols)
+{
+    CU(cudaMemcpy2DAsync(dst, (size_t)cols * sizeof(float), src, (size_t)ld * sizeof(float),
+                         (size_t)cols * sizeof(float), rows, cudaMemcpyDefault, c->stream));
+    return 0;
+}
+
+// Validate the freshly uploaded networks: finite entries, exact symmetry.
+int validate(panda_ctx *c)
+{
+    Dev &d = c->d;
+    int flags[4];
+    CU(cudaMemsetAsync(c->d_flags, 0, 4 * sizeof(int), c->stream));
+    CU(launch_check_finite_sym(d.W[c->cur], c->T, c->G, c->Gp, false, c->d_flags, c->stream));
+    CU(launch_check_finite_sym(d.Poff, c->T, c->T, c->Tp, true, c->d_flags, c->stream));
+    CU(launch_check_finite_sym(d.Coff, c->G, c->G, c->Gp, true, c->d_flags, c->stream));
+    CU(cudaMemcpyAsync(flags, c->d_flags, 4 * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    if (flags[0])
+        return set_err(c, PANDA_ENONFINITE, "an input network has a non-finite entry");
+    if (flags[1])
+        return set_err(c, PANDA_EASYM, "P0 or C0 is not exactly symmetric");
+    return 0;
+}
+
+int zscore_all(panda_ctx *c)
+{
+    Dev &d = c->d;
+    struct { float *X; int rows, cols, ld; const char *name; } nets[3] = {
+        {d.W[c->cur], c->T, c->G, c->Gp, "W0"},
+        {d.Poff, c->T, c->T, c->Tp, "P0"},
+        {d.Coff, c->G, c->G, c->Gp, "C0"}};
+    for (auto &n : nets) {
+        double st[2];
+        CU(launch_zscore(n.X, n.rows, n.cols, n.ld, c->d_stats, c->d_partials, c->stream));
+        CU(cudaMemcpyAsync(st, c->d_stats, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        if (!(st[1] > 0.0))
+            return set_err(c, PANDA_EDEGENERATE,
+                           std::string(n.name) + " has zero standard deviation; its Z-score is undefined");
+        if (!std::isfinite(st[0]) || !std::isfinite(st[1]))
+            return set_err(c, PANDA_ENONFINITE, std::string(n.name) + " statistics are not finite");
+    }
+    return 0;
+}
+
+// From full W (in W[cur]), P and C (diagonals in place): strip diagonals,
+// transposed W, squared norms, split copies.
+int derive_state(panda_ctx *c, bool split_diag)
+{
+    Dev &d = c->d;
+    if (split_diag) {
+        CU(launch_split_diag(d.Poff, c->T, c->Tp, d.pd, d.pdf, c->stream));
+        CU(launch_split_diag(d.Coff, c->G, c->Gp, d.cd, d.cdf, c->stream));
+    }
+    CU(launch_transpose(d.W[c->cur], c->Tp, c->Gp, d.Wt[c->cur], c->stream));
+    CU(launch_row_norms(d.W[c->cur], c->T, c->G, c->Gp, nullptr, d.rsqW, c->stream));
+    CU(launch_col_norms(d.W[c->cur], c->T, c->G, c->Gp, d.csqW, c->stream));
+    CU(launch_row_norms(d.Poff, c->T, c->T, c->Tp, d.pd, d.rsqP, c->stream));
+    CU(launch_row_norms(d.Coff, c->G, c->G, c->Gp, d.cd, d.csqC, c->stream));
+    if (c->prec == PANDA_BF16X3)
+        CU(tc_prepare(d, c->stream));
+    return 0;
+}
+
+void drop_graphs(panda_ctx *c)
+{
+    for (auto &g : c->gexec)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+int n_kernels(const panda_ctx *c) { return c->prec == PANDA_BF16X3 ? TC_KERNELS : SIMT_KERNELS; }
+
+const char *kernel_name(const panda_ctx *c, int i)
+{
+    return c->prec == PANDA_BF16X3 ? TC_KERNEL_NAMES[i] : SIMT_KERNEL_NAMES[i];
+}
+
+// slot: which iteration of a graph (or chunk) this is, for the timing events
+int launch_iteration(panda_ctx *c, int cur, int slot)
+{
+    KernelEvents ke{c->prof ? c->ev.data() + (size_t)slot * (n_kernels(c) + 1) : nullptr, 0};
+    cudaError_t e = c->prec == PANDA_BF16X3 ? launch_iteration_tc(c->d, cur, c->stream, ke)
+                                            : launch_iteration_simt(c->d, cur, c->stream, ke);
+    if (e != cudaSuccess)
+        return set_err(c, PANDA_ECUDA, std::string("iteration launch: ") + cudaGetErrorString(e));
+    return 0;
+}
+
+int ensure_graph(panda_ctx *c, int cur)
+{
+    if (c->gexec[cur])
+        return 0;
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = 0;
+    for (int k = 0; k < c->graph_iters && !rc; ++k)
+        rc = launch_iteration(c, cur ^ (k & 1), k);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc) {
+        if (g)
+            cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess)
+        return set_err(c, PANDA_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&c->gexec[cur], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->gexec[cur] = nullptr;
+        return set_err(c, PANDA_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    return 0;
+}
+
+int fill_e2(panda_ctx *c, float alpha)
+{
+    if (c->e2_alpha == alpha)
+        return 0;
+    std::vector<double> tab(HIST_CAP + 1);
+    for (int t = 0; t <= HIST_CAP; ++t)
+        tab[t] = std::exp(2.0 * (double)alpha * (double)t);  // e^{2 alpha t} of Eq. 6
+    CU(cudaMemcpyAsync(c->d.e2tab, tab.data(), tab.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    c->e2_alpha = alpha;
+    return 0;
+}
+
+// Run up to max_iter iterations (stopping early when h < tol).
+int drive(panda_ctx *c, float alpha, double tol, int max_iter, bool use_graph, int *n_done)
+{
+    *n_done = 0;
+    if (max_iter <= 0)
+        return 0;
+    int rc = fill_e2(c, alpha);
+    if (rc)
+        return rc;
+    Ctl &h = *c->h_ctl;
+    const int start = h.iters;
+    if ((long long)start + max_iter > (long long)HIST_CAP)
+        return set_err(c, PANDA_EINVAL, "iteration count would exceed the supported maximum (65536)");
+    h.active = 1;
+    h.stop_at = start + max_iter;
+    h.status = 0;
+    h.converged = 0;
+    h.alpha = alpha;
+    h.tol = tol;
+    if ((rc = push_ctl(c)))
+        return rc;
+    const int K = c->graph_iters;
+    while (true) {
+        const int before = h.iters;
+        const int cur = c->cur ^ ((before - start) & 1);
+        if (use_graph && K > 0 && c->stream != nullptr) {  // the legacy NULL stream cannot be captured
+            if ((rc = ensure_graph(c, cur)))
+                return rc;
+            CU(cudaGraphLaunch(c->gexec[cur], c->stream));
+        } else {
+            int chunk = K > 0 ? K : 1;
+            if (chunk > h.stop_at - before)
+                chunk = h.stop_at - before;
+            for (int k = 0; k < chunk; ++k)
+                if ((rc = launch_iteration(c, cur ^ (k & 1), k)))
+                    return rc;
+        }
+        if ((rc = sync_ctl(c)))
+            return rc;
+        if (c->prof) {  // iterations that did work in this chunk: their kernel times
+            const int nk = n_kernels(c);
+            for (int k = 0; k < h.iters - before; ++k) {
+                cudaEvent_t *e = c->ev.data() + (size_t)k * (nk + 1);
+                for (int q = 0; q < nk; ++q) {
+                    float ms = 0.0f;
+                    CU(cudaEventElapsedTime(&ms, e[q], e[q + 1]));
+                    c->k_ms[q] += ms;
+                    c->k_launches[q] += 1;
+                }
+            }
+        }
+        if (!h.active)
+            break;
+    }
+    *n_done = h.iters - start;
+    c->cur ^= (*n_done & 1);
+    if (h.status & ST_NONFINITE)
+        return set_err(c, PANDA_ENONFINITE, "the state became non-finite");
+    if (h.status & ST_TIMEOUT)
+        return set_err(c, PANDA_ETIMEOUT, "a bounded device wait expired");
+    return 0;
+}
+
+int check_ctx(const panda_ctx *c) { return c ? 0 : PANDA_EINVAL; }
+
+void free_all(panda_ctx *c)
+{
+    if (!c)
+        return;
+    drop_graphs(c);
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    for (void *p : c->allocs)
+        cudaFree(p);
+    c->allocs.clear();
+    if (c->h_ctl)
+        cudaFreeHost(c->h_ctl);
+    for (auto &ev : c->ev)
+        if (ev)
+            cudaEventDestroy(ev);
+    c->ev.clear();
+    if (c->own_stream && c->stream)
+        cudaStreamDestroy(c->stream);
+}
+
+int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P0, const float *C0,
+                  const panda_opts *o, void *stream, bool device_ptrs)
+{
+    if (!out)
+        return set_err(nullptr, PANDA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (T <= 0 || G <= 0)
+        return set_err(nullptr, PANDA_EINVAL, "T and G must be positive");
+    if (!W0 || !P0 || !C0)
+        return set_err(nullptr, PANDA_EINVAL, "W0, P0 and C0 must not be NULL");
+    if ((long long)G > 46000 || (long long)T > 46000)
+        return set_err(nullptr, PANDA_EINVAL, "T and G must be at most 46000");
+    panda_opts opts;
+    panda_default_opts(&opts);
+    if (o)
+        opts = *o;
+    if (opts.prec != PANDA_FP32 && opts.prec != PANDA_BF16X3)
+        return set_err(nullptr, PANDA_EUNSUPPORTED, "precision mode not built (FP32 and BF16X3 are)");
+    if (opts.diag < 0 || opts.diag > 2 || opts.t0 < 0 || opts.t0 >= HIST_CAP || opts.graph_iters < 0)
+        return set_err(nullptr, PANDA_EINVAL, "bad option value");
+    if (opts.prec == PANDA_BF16X3 && !tc_supported())
+        return set_err(nullptr, PANDA_EUNSUPPORTED, "BF16X3 needs an sm_103 device");
+
+    panda_ctx *c = new panda_ctx();
+    c->T = T; c->G = G;
+    c->Tp = round_up(T, TILE); c->Gp = round_up(G, TILE);
+    c->nbT = c->Tp / TILE; c->nbG = c->Gp / TILE;
+    c->prec = opts.prec; c->diag = opts.diag; c->normalize = opts.normalize;
+    c->graph_iters = (opts.graph_iters + 1) & ~1;  // even: a graph returns to its start buffer
+    c->limit = alloc_limit_from_env();
+    int rc = 0;
+    auto fail = [&](int code) {
+        std::string msg = c->err;
+        free_all(c);
+        delete c;
+        g_create_error = msg;
+        return code;
+    };
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) {
+        c->err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return fail(PANDA_ECUDA);
+    }
+    if (device_ptrs) {
+        c->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            c->err = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            return fail(PANDA_ECUDA);
+        }
+        c->own_stream = true;
+    }
+    e = cudaMallocHost(&c->h_ctl, sizeof(Ctl));
+    if (e != cudaSuccess) {
+        c->err = std::string("cudaMallocHost: ") + cudaGetErrorString(e);
+        return fail(PANDA_ENOMEM);
+    }
+    std::memset(c->h_ctl, 0, sizeof(Ctl));
+    c->h_ctl->iters = opts.t0;
+    c->ev.resize((size_t)(c->graph_iters > 0 ? c->graph_iters : 1) * 17, nullptr);
+    for (auto &ev : c->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
+            c->err = std::string("cudaEventCreate: ") + cudaGetErrorString(e);
+            return fail(PANDA_ECUDA);
+        }
+    if ((rc = plan_memory(c)))
+        return fail(rc);
+    if ((rc = upload(c, c->d.W[0], c->Gp, W0, T, G)) || (rc = upload(c, c->d.Poff, c->Tp, P0, T, T)) ||
+        (rc = upload(c, c->d.Coff, c->Gp, C0, G, G)))
+        return fail(rc);
+    if ((rc = validate(c)))
+        return fail(rc);
+    if (c->normalize && (rc = zscore_all(c)))
+        return fail(rc);
+    if ((rc = derive_state(c, true)) || (rc = push_ctl(c)))
+        return fail(rc);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->err = std::string("create: ") + cudaGetErrorString(e);
+        return fail(PANDA_ECUDA);
+    }
+    *out = c;
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int panda_precision_supported(int prec)
+{
+    if (prec == PANDA_FP32) {
+        int n = 0;
+        return cudaGetDeviceCount(&n) == cudaSuccess && n > 0;
+    }
+    if (prec == PANDA_BF16X3)
+        return tc_supported() ? 1 : 0;
+    return 0;
+}
+
+void panda_default_opts(panda_opts *o)
+{
+    if (!o)
+        return;
+    o->prec = PANDA_FP32;
+    o->diag = PANDA_DIAG_D1;
+    o->normalize = 1;
+    o->t0 = 0;
+    o->graph_iters = 8;
+}
+
+int panda_create(panda_ctx **out, int T, int G, const float *W0, const float *P0, const float *C0,
+                 const panda_opts *o)
+{
+    return create_common(out, T, G, W0, P0, C0, o, nullptr, false);
+}
+
+int panda_create_device(panda_ctx **out, int T, int G, const float *dW0, const float *dP0,
+                        const float *dC0, const panda_opts *o, void *stream)
+{
+    return create_common(out, T, G, dW0, dP0, dC0, o, stream, true);
+}
+
+int panda_step(panda_ctx *c, float alpha, double *h_out)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    if (!(alpha >= 0.0f && alpha <= 1.0f))
+        return set_err(c, PANDA_EINVAL, "alpha must be in [0, 1]");
+    int n = 0;
+    int rc = drive(c, alpha, -1.0, 1, false, &n);
+    if (rc)
+        return rc;
+    if (h_out)
+        *h_out = c->h_ctl->h_last;
+    return 0;
+}
+
+int panda_run(panda_ctx *c, float alpha, double tol, int max_iter, int *iters_out, double *h_last)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    if (!(alpha >= 0.0f && alpha <= 1.0f))
+        return set_err(c, PANDA_EINVAL, "alpha must be in [0, 1]");
+    if (!(tol >= 0.0) || max_iter < 0)
+        return set_err(c, PANDA_EINVAL, "tol must be >= 0 and max_iter >= 0");
+    int n = 0;
+    int rc = drive(c, alpha, tol, max_iter, c->graph_iters > 0, &n);
+    if (iters_out)
+        *iters_out = n;
+    if (h_last)
+        *h_last = c->h_ctl->h_last;
+    if (rc)
+        return rc;
+    return c->h_ctl->converged ? PANDA_OK : PANDA_NOT_CONVERGED;
+}
+
+static int get_impl(panda_ctx *c, float *W, float *P, float *C)
+{
+    Dev &d = c->d;
+    if (W) {
+        int rc = download(c, W, d.W[c->cur], c->Gp, c->T, c->G);
+        if (rc)
+            return rc;
+    }
+    struct { float *dst; const float *src; const double *diag; int n, ld; } nets[2] = {
+        {P, d.Poff, d.pd, c->T, c->Tp}, {C, d.Coff, d.cd, c->G, c->Gp}};
+    for (auto &n : nets) {
+        if (!n.dst)
+            continue;
+        int rc = download(c, n.dst, n.src, n.ld, n.n, n.n);
+        if (rc)
+            return rc;
+        // diagonal entries, rounded from the FP64 diagonal
+        std::vector<double> dg(n.n);
+        CU(cudaMemcpyAsync(dg.data(), n.diag, n.n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+        std::vector<float> f(n.n);
+        for (int i = 0; i < n.n; ++i)
+            f[i] = (float)dg[i];
+        CU(cudaMemcpy2DAsync(n.dst, (size_t)(n.n + 1) * sizeof(float), f.data(), sizeof(float),
+                             sizeof(float), n.n, cudaMemcpyDefault, c->stream));
+        CU(cudaStreamSynchronize(c->stream));  // f is released at the end of this scope
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    return 0;
+}
+
+int panda_get(panda_ctx *c, float *W, float *P, float *C)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    return get_impl(c, W, P, C);
+}
+
+int panda_get_device(panda_ctx *c, float *dW, float *dP, float *dC)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    return get_impl(c, dW, dP, dC);
+}
+
+int panda_get_state(panda_ctx *c, float *W, float *P, float *C, int *t)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    int rc = get_impl(c, W, P, C);
+    if (!rc && t)
+        *t = c->h_ctl->iters;
+    return rc;
+}
+
+int panda_set_state(panda_ctx *c, const float *W, const float *P, const float *C, int t)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    if (!W || !P || !C || t < 0 || t >= HIST_CAP)
+        return set_err(c, PANDA_EINVAL, "W, P, C must be non-NULL and 0 <= t < 65536");
+    drop_graphs(c);
+    Dev &d = c->d;
+    c->cur = 0;
+    int rc;
+    if ((rc = upload(c, d.W[0], c->Gp, W, c->T, c->G)) || (rc = upload(c, d.Poff, c->Tp, P, c->T, c->T)) ||
+        (rc = upload(c, d.Coff, c->Gp, C, c->G, c->G)))
+        return rc;
+    if ((rc = validate(c)) || (rc = derive_state(c, true)))
+        return rc;
+    c->h_ctl->iters = t;
+    c->h_ctl->active = 0;
+    c->h_ctl->status = 0;
+    if ((rc = push_ctl(c)))
+        return rc;
+    CU(cudaStreamSynchronize(c->stream));
+    return 0;
+}
+
+// ---- checkpoints -------------------------------------------------------------
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int version, T, G, prec, diag, iters;
+    int pad;
+};
+
+struct CkptItem {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<CkptItem> ckpt_items(panda_ctx *c)
+{
+    Dev &d = c->d;
+    const size_t Tp = c->Tp, Gp = c->Gp;
+    return {{d.W[c->cur], Tp * Gp * 4}, {d.Poff, Tp * Tp * 4}, {d.Coff, Gp * Gp * 4},
+            {d.pd, Tp * 8},   {d.cd, Gp * 8},   {d.rsqP, Tp * 4}, {d.csqC, Gp * 4},
+            {d.rsqW, Tp * 4}, {d.csqW, Gp * 4}, {d.hist, (size_t)HIST_CAP * 8}};
+}
+}  // namespace
+
+long long panda_checkpoint_bytes(const panda_ctx *cc)
+{
+    if (!cc)
+        return 0;
+    panda_ctx *c = const_cast<panda_ctx *>(cc);
+    long long n = sizeof(CkptHeader);
+    for (auto &it : ckpt_items(c))
+        n += (long long)it.bytes;
+    return n;
+}
+
+int panda_save(panda_ctx *c, void *buf, long long bytes)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    if (!buf || bytes < panda_checkpoint_bytes(c))
+        return set_err(c, PANDA_EINVAL, "checkpoint buffer too small");
+    CkptHeader h{};
+    std::memcpy(h.magic, "PANDAGB", 8);
+    h.version = 1; h.T = c->T; h.G = c->G; h.prec = c->prec; h.diag = c->diag; h.iters = c->h_ctl->iters;
+    char *p = static_cast<char *>(buf);
+    std::memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    for (auto &it : ckpt_items(c)) {
+        CU(cudaMemcpyAsync(p, it.dev, it.bytes, cudaMemcpyDeviceToHost, c->stream));
+        p += it.bytes;
+    }
+    CU(cudaStreamSynchronize(c->stream));
+    return 0;
+}
+
+int panda_load(panda_ctx *c, const void *buf, long long bytes)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    if (!buf || bytes < panda_checkpoint_bytes(c))
+        return set_err(c, PANDA_EINVAL, "checkpoint buffer too small");
+    CkptHeader h;
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, "PANDAGB", 8) || h.version != 1 || h.T != c->T || h.G != c->G ||
+        h.prec != c->prec || h.diag != c->diag)
+        return set_err(c, PANDA_EINVAL, "checkpoint does not match this context");
+    drop_graphs(c);
+    const char *p = static_cast<const char *>(buf) + sizeof h;
+    for (auto &it : ckpt_items(c)) {
+        CU(cudaMemcpyAsync(it.dev, p, it.bytes, cudaMemcpyHostToDevice, c->stream));
+        p += it.bytes;
+    }
+    Dev &d = c->d;
+    CU(launch_transpose(d.W[c->cur], c->Tp, c->Gp, d.Wt[c->cur], c->stream));
+    CU(launch_diag_to_float(d.pd, d.pdf, c->T, c->stream));
+    CU(launch_diag_to_float(d.cd, d.cdf, c->G, c->stream));
+    if (c->prec == PANDA_BF16X3)
+        CU(tc_prepare(d, c->stream));
+    c->h_ctl->iters = h.iters;
+    c->h_ctl->active = 0;
+    c->h_ctl->status = 0;
+    int rc = push_ctl(c);
+    if (rc)
+        return rc;
+    CU(cudaStreamSynchronize(c->stream));
+    return 0;
+}
+
+int panda_get_history(panda_ctx *c, double *hh, int cap, int *n)
+{
+    if (check_ctx(c) || (cap > 0 && !hh))
+        return PANDA_EINVAL;
+    int m = c->h_ctl->iters;
+    if (n)
+        *n = m;
+    int k = m < cap ? m : cap;
+    if (k > HIST_CAP)
+        k = HIST_CAP;
+    if (k > 0) {
+        CU(cudaMemcpyAsync(hh, c->d.hist, (size_t)k * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return 0;
+}
+
+int panda_info(const panda_ctx *c, int *T, int *G, int *prec, int *t)
+{
+    if (!c)
+        return PANDA_EINVAL;
+    if (T) *T = c->T;
+    if (G) *G = c->G;
+    if (prec) *prec = c->prec;
+    if (t) *t = c->h_ctl->iters;
+    return 0;
+}
+
+long long panda_device_bytes(const panda_ctx *c) { return c ? c->bytes : 0; }
+
+int panda_set_profiling(panda_ctx *c, int on)
+{
+    if (check_ctx(c))
+        return PANDA_EINVAL;
+    if (c->prof != (on != 0))
+        drop_graphs(c);  // graphs are captured with or without the timing events
+    c->prof = on != 0;
+    for (int q = 0; q < 16; ++q) {
+        c->k_ms[q] = 0.0;
+        c->k_launches[q] = 0;
+    }
+    return 0;
+}
+
+int panda_kernel_count(const panda_ctx *c) { return c ? n_kernels(c) : 0; }
+
+int panda_kernel_stats(const panda_ctx *c, int i, char *name, int name_cap, double *total_ms,
+                       long long *launches)
+{
+    if (!c || i < 0 || i >= n_kernels(c))
+        return PANDA_EINVAL;
+    if (name && name_cap > 0) {
+        std::strncpy(name, kernel_name(c, i), (size_t)name_cap - 1);
+        name[name_cap - 1] = 0;
+    }
+    if (total_ms)
+        *total_ms = c->k_ms[i];
+    if (launches)
+        *launches = c->k_launches[i];
+    return 0;
+}
+
+void *panda_stream(const panda_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+const char *panda_last_error(const panda_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void panda_destroy(panda_ctx *c)
+{
+    if (!c)
+        return;
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Internal declarations of libpanda_gb300 (not part of the C ABI).
+//
+// Device layout (all row-major, every dimension padded with zeros to a
+// multiple of 128 so that GEMM tiles never need bounds checks in their main
+// loops; the epilogues mask by the true T and G):
+//   W[2]   Tp x Gp  fp32   regulatory network, ping-pong (current / next)
+//   Wt[2]  Gp x Tp  fp32   its transpose, written by the same epilogue
+//   Poff   Tp x Tp  fp32   P with a zero diagonal (diagonal kept in pd)
+//   Coff   Gp x Gp  fp32   C with a zero diagonal (diagonal kept in cd)
+//   pd, cd          fp64   diagonals of P and C
+//   rsqP, csqC      fp32   |P_i.|^2 and |C_.j|^2, diagonal included
+//   rsqW, csqW      fp32   |W_i.|^2 and |W_.j|^2 of the current W
+// plus per-tile partial sums (scratch) and a small control block.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+namespace panda {
+
+constexpr int TILE = 128;          // padding granule and SIMT tile edge
+constexpr int HIST_CAP = 1 << 16;  // iterations whose h is kept on the device
+
+// Device control block, read by every kernel of an iteration.
+struct Ctl {
+    int active;     // kernels of an iteration do their work only while 1
+    int iters;      // iterations done so far (the next one uses t = iters + 1)
+    int stop_at;    // iteration count at which the current run stops
+    int status;     // bit 0: non-finite state; bit 1: device wait timed out
+    int converged;  // 1 when the last iteration gave h < tol
+    float alpha;
+    float pad0;
+    double tol;
+    double h_last;
+};
+
+enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
+
+// Pointers and shapes handed to kernels by value.
+struct Dev {
+    int T, G, Tp, Gp, nbT, nbG;  // true sizes, padded sizes, 128-blocks
+    int diag;                    // panda_diag
+    float *W[2], *Wt[2];
+    float *Poff, *Coff;
+    double *pd, *cd;
+    float *pdf, *cdf;            // FP32 copies of the diagonals for epilogues
+    float *rsqP, *csqC, *rsqW, *csqW;
+    // scratch
+    float *Rn;                   // Tp x Gp  P_off . W  (SIMT path)
+    float *wrow_part;            // nbG x Tp
+    float *wcol_part;            // nbT x Gp
+    double *hpart;               // nbT * nbG
+    float *ps_sum, *ps_sq, *ps_vsq;  // nbT x Tp  row partials of P'
+    float *cs_sum, *cs_sq, *cs_vsq;  // nbG x Gp  row partials of C'
+    Ctl *ctl;
+    double *hist;                // HIST_CAP
+    double *e2tab;               // HIST_CAP + 1: e^{2 alpha t}, computed on the host
+    // BF16 split copies (tensor-core path only; NULL otherwise)
+    __nv_bfloat16 *Wh[2], *Wl[2], *Wth[2], *Wtl[2];
+    __nv_bfloat16 *Ph, *Pl, *Ch, *Cl;
+    float *pacc;                 // split-K partial accumulators of W'.W'^T
+    int tc_ksplit;               // split-K factor of the P product
+};
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ inline int round_up(int a, int b) { return ceil_div(a, b) * b; }
+
+// Eq. 1 from a numerator and the two squared norms (FP32, IEEE sqrt and
+// division); 0 when the denominator is 0 (both vectors zero).
+__device__ __forceinline__ float tanimoto_f(float num, float nx, float ny)
+{
+    float den = sqrtf((nx + ny) - fabsf(num));
+    return den > 0.0f ? num / den : 0.0f;
+}
+
+// ---- launchers (k_setup.cu) ------------------------------------------------
+cudaError_t launch_check_finite_sym(const float *X, int rows, int cols, int ld, bool sym,
+                                    int *flags, cudaStream_t s);
+cudaError_t launch_zscore(float *X, int rows, int cols, int ld, double *stats, double *partials,
+                          cudaStream_t s);
+cudaError_t launch_split_diag(float *X, int n, int ld, double *d, float *df, cudaStream_t s);
+cudaError_t launch_transpose(const float *X, int rows_p, int cols_p, float *Y, cudaStream_t s);
+cudaError_t launch_row_norms(const float *X, int rows, int cols, int ld, const double *diag,
+                             float *out, cudaStream_t s);
+cudaError_t launch_col_norms(const float *X, int rows, int cols, int ld, float *out,
+                             cudaStream_t s);
+cudaError_t launch_diag_to_float(const double *d, float *df, int n, cudaStream_t s);
+cudaError_t launch_scan_nonfinite(const float *X, long long n, int *flag, cudaStream_t s);
+
+// Optional per-kernel timing: when ev is not NULL, ev[0] is recorded before the
+// first kernel of the iteration and ev[k + 1] after kernel k.
+struct KernelEvents {
+    cudaEvent_t *ev;
+    int n;  // events recorded so far
+    void mark(cudaStream_t s)
+    {
+        if (ev)
+            cudaEventRecord(ev[n++], s);
+    }
+};
+
+// ---- one iteration, FP32 SIMT path (k_simt.cu) -----------------------------
+constexpr int SIMT_KERNELS = 6;
+extern const char *const SIMT_KERNEL_NAMES[SIMT_KERNELS];
+cudaError_t launch_iteration_simt(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
+// shared tail of every path: diagonals, norms of P and C, h, stop test
+cudaError_t launch_fin_tail(const Dev &d, cudaStream_t s, KernelEvents &ke);
+
+// ---- tensor-core path (k_tc.cu) --------------------------------------------
+constexpr int TC_KERNELS = 6;
+extern const char *const TC_KERNEL_NAMES[TC_KERNELS];
+bool tc_supported();
+cudaError_t tc_prepare(Dev &d, cudaStream_t s);  // build the split copies of the state
+cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
+
+}  // namespace panda

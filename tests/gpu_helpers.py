@@ -1,0 +1,84 @@
+"""Shared pieces of the GPU parity tests: run the CUDA library and the oracle on
+the same seeded inputs and compare element by element.
+
+Tolerances (FP32 epilogues; derivation in the design notes):
+  * W: max |W_gpu - W_oracle| <= 1e-5 on the FP32 path, 1e-4 on BF16X3.
+  * off-diagonal P and C: max abs error <= tol_off * max(1, max |X|), with
+    tol_off = 2e-5 (FP32) and 2e-4 (BF16X3): entries are similarities whose
+    scale grows with the vector length.
+  * diagonals of P and C: relative error <= 2e-5 (FP32) / 2e-4 (BF16X3); they
+    grow like e^{2 alpha t}.
+  * iteration counts identical, unless the oracle's h lands within 1e-6 of tol
+    at the stopping iteration, in which case both run the same fixed count.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from paper_1507_07039_gb300 import synth
+
+TOL = {
+    0: dict(W=1e-5, off=2e-5, diag=2e-5),  # PANDA_FP32
+    1: dict(W=1e-4, off=2e-4, diag=2e-4),  # PANDA_BF16X3
+}
+
+
+def f32_alpha(alpha: float) -> float:
+    """The library takes alpha as FP32; the oracle is given the same value."""
+    return float(np.float32(alpha))
+
+
+def gpu_run(W0, P0, C0, prec=0, alpha=0.1, tol=1e-3, max_iter=200, normalize=True, diag=0,
+            graph_iters=8):
+    from paper_1507_07039_gb300 import panda
+    with panda.PandaContext(W0, P0, C0, prec=prec, diag=diag, normalize=normalize,
+                            graph_iters=graph_iters) as ctx:
+        conv, n, h = ctx.run(alpha, tol, max_iter)
+        W, P, C = ctx.get()
+        hist = ctx.history()
+    return dict(W=W, P=P, C=C, iters=n, hist=hist, converged=conv)
+
+
+def oracle_run(orc, W0, P0, C0, alpha=0.1, tol=1e-3, max_iter=200, normalize=True, diag=0):
+    W, P, C = (np.asarray(x, np.float64) for x in (W0, P0, C0))
+    if normalize:
+        W, P, C = orc.normalize(W, P, C)
+    W, P, C, n, hist, conv = orc.run(W, P, C, f32_alpha(alpha), tol, max_iter, 0, diag)
+    return dict(W=W, P=P, C=C, iters=n, hist=hist, converged=conv)
+
+
+def errors(g, o):
+    """Max abs error of W, of the off-diagonals of P and C (relative to their
+    scale), and max relative error of the diagonals."""
+    out = {"W": float(np.max(np.abs(g["W"].astype(np.float64) - o["W"])))}
+    for name in ("P", "C"):
+        x, y = g[name].astype(np.float64), o[name]
+        n = x.shape[0]
+        off = ~np.eye(n, dtype=bool)
+        scale = max(1.0, float(np.max(np.abs(y[off])))) if n > 1 else 1.0
+        out[name + "off"] = float(np.max(np.abs(x[off] - y[off]))) / scale if n > 1 else 0.0
+        dx, dy = np.diag(x), np.diag(y)
+        out[name + "diag"] = float(np.max(np.abs(dx - dy) / np.maximum(np.abs(dy), 1.0)))
+    return out
+
+
+def assert_parity(g, o, prec=0, what=""):
+    t = TOL[prec]
+    e = errors(g, o)
+    assert e["W"] <= t["W"], f"{what} W err {e['W']:.3e} > {t['W']:.1e} ({e})"
+    for k in ("Poff", "Coff"):
+        assert e[k] <= t["off"], f"{what} {k} err {e[k]:.3e} > {t['off']:.1e} ({e})"
+    for k in ("Pdiag", "Cdiag"):
+        assert e[k] <= t["diag"], f"{what} {k} err {e[k]:.3e} > {t['diag']:.1e} ({e})"
+    return e
+
+
+def inputs(name_or_wl):
+    wl = synth.get(name_or_wl) if isinstance(name_or_wl, str) else name_or_wl
+    return synth.make_inputs(wl)
+
+
+def random_symmetric(rng, n):
+    X = rng.standard_normal((n, n))
+    X = (X + X.T) / 2
+    return X.astype(np.float32)

@@ -1,0 +1,196 @@
+"""CUDA library against the FP64 oracle, through the C ABI (needs a GB300)."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import gpu_helpers as gh
+from oracle.oracle import Oracle
+from paper_1507_07039_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+PRECS = [0]  # PANDA_FP32 (PANDA_BF16X3 joins once its kernels exist)
+
+
+@pytest.fixture(scope="module")
+def orc():
+    o = Oracle()
+    o.set_threads(os.cpu_count() or 1)
+    return o
+
+
+@pytest.fixture(scope="module")
+def panda():
+    from paper_1507_07039_gb300 import panda as p
+    return p
+
+
+def _fixed_or_same_count(o, tol):
+    """True when the oracle's stop decision sits within 1e-6 of tol."""
+    return bool(np.any(np.abs(o["hist"] - tol) < 1e-6))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_small_network_full_trajectory(orc, prec):
+    """64 TFs x 256 genes, alpha 0.1, tol 1e-3, up to 200 iterations."""
+    W0, P0, C0 = gh.inputs("small64x256")
+    o = gh.oracle_run(orc, W0, P0, C0, 0.1, 1e-3, 200)
+    g = gh.gpu_run(W0, P0, C0, prec, 0.1, 1e-3, 200)
+    if _fixed_or_same_count(o, 1e-3):
+        o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, o["iters"])
+        g = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, o["iters"])
+    assert g["iters"] == o["iters"] and g["converged"] == o["converged"]
+    np.testing.assert_allclose(g["hist"], o["hist"], rtol=1e-4 if prec else 1e-5, atol=1e-9)
+    gh.assert_parity(g, o, prec, "small")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_mid_network_fixed_iterations(orc, prec):
+    """250 TFs x 2100 genes (two ragged tile edges), 12 fixed iterations."""
+    W0, P0, C0 = gh.inputs("mid250x2100")
+    o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 12)
+    g = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 12)
+    assert g["iters"] == 12 and not g["converged"]
+    gh.assert_parity(g, o, prec, "mid")
+
+
+EDGE_SHAPES = [(1, 1), (1, 5), (3, 1), (2, 3), (5, 130), (130, 7), (129, 257), (128, 128), (200, 385)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("T,G", EDGE_SHAPES)
+def test_edge_shapes(orc, prec, T, G):
+    """Tiny, single-node and ragged networks, without normalisation, 3 iterations."""
+    rng = np.random.default_rng(1000 * T + G)
+    W0 = rng.standard_normal((T, G)).astype(np.float32)
+    P0, C0 = gh.random_symmetric(rng, T), gh.random_symmetric(rng, G)
+    o = gh.oracle_run(orc, W0, P0, C0, 0.2, 0.0, 3, normalize=False)
+    g = gh.gpu_run(W0, P0, C0, prec, 0.2, 0.0, 3, normalize=False)
+    gh.assert_parity(g, o, prec, f"{T}x{G}")
+
+
+@pytest.mark.parametrize("diag", [1, 2])
+def test_other_diagonal_rules(orc, diag):
+    W0, P0, C0 = gh.inputs(synth.custom(40, 150, 77, n_samples=30, n_factors=3))
+    o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 6, diag=diag)
+    g = gh.gpu_run(W0, P0, C0, 0, 0.1, 0.0, 6, diag=diag)
+    gh.assert_parity(g, o, 0, f"diag rule {diag}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_identity_priors(orc, prec):
+    """The paper's Table I shape: P = C = I, random W."""
+    W0, P0, C0 = gh.inputs(synth.table1(125))
+    o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 10)
+    g = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 10)
+    gh.assert_parity(g, o, prec, "identity priors")
+
+
+def test_alpha_zero_leaves_networks_unchanged(panda):
+    W0, P0, C0 = gh.inputs("small64x256")
+    with panda.PandaContext(W0, P0, C0) as ctx:
+        W1, P1, C1 = ctx.get()
+        for _ in range(3):
+            assert ctx.step(0.0) == 0.0
+        W2, P2, C2 = ctx.get()
+    assert np.array_equal(W1, W2) and np.array_equal(P1, P2) and np.array_equal(C1, C2)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_symmetry_and_determinism(prec):
+    W0, P0, C0 = gh.inputs("mid250x2100")
+    a = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 5)
+    b = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 5, graph_iters=0)
+    for k in ("W", "P", "C"):
+        assert np.array_equal(a[k], b[k]), f"{k} differs between two runs"
+    assert np.array_equal(a["P"], a["P"].T) and np.array_equal(a["C"], a["C"].T)
+    assert np.all(a["hist"] >= 0)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_checkpoint_resume_is_bitwise(panda, prec):
+    W0, P0, C0 = gh.inputs("small64x256")
+    with panda.PandaContext(W0, P0, C0, prec=prec) as a:
+        a.run(0.1, 0.0, 4)
+        blob = panda.panda_save(a.h)
+        a.run(0.1, 0.0, 5)
+        ref = a.get()
+        ref_hist = a.history()
+    with panda.PandaContext(W0, P0, C0, prec=prec) as b:
+        panda.panda_load(b.h, blob)
+        assert b.info()[3] == 4
+        b.run(0.1, 0.0, 5)
+        got = b.get()
+        hist = b.history()
+    for x, y in zip(ref, got):
+        assert np.array_equal(x, y)
+    assert np.array_equal(ref_hist, hist)
+
+
+def test_set_state_continues_close(panda):
+    W0, P0, C0 = gh.inputs("small64x256")
+    with panda.PandaContext(W0, P0, C0) as a:
+        a.run(0.1, 0.0, 3)
+        W, P, C, t = panda.panda_get_state(a.h, 64, 256)
+        a.run(0.1, 0.0, 3)
+        ref = a.get()
+    with panda.PandaContext(W0, P0, C0) as b:
+        panda.panda_set_state(b.h, W, P, C, t)
+        b.run(0.1, 0.0, 3)
+        got = b.get()
+    assert np.max(np.abs(ref[0] - got[0])) < 1e-5
+
+
+def test_device_pointer_create_matches_host(panda):
+    import torch
+    W0, P0, C0 = gh.inputs("small64x256")
+    dW, dP, dC = (torch.from_numpy(x).cuda() for x in (W0, P0, C0))
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    with panda.PandaContext(dW, dP, dC, device=True, stream=stream) as a:
+        a.run(0.1, 0.0, 4)
+        oW = torch.empty_like(dW)
+        panda.panda_get_device(a.h, oW, None, None)
+        got = oW.cpu().numpy()
+    ref = gh.gpu_run(W0, P0, C0, 0, 0.1, 0.0, 4)["W"]
+    assert np.array_equal(got, ref)
+
+
+def test_error_codes(panda):
+    W0, P0, C0 = gh.inputs("small64x256")
+    bad = C0.copy()
+    bad[3, 7] += 1.0
+    with pytest.raises(panda.PandaError) as e:
+        panda.PandaContext(W0, P0, bad)
+    assert e.value.code == -5
+    nan = W0.copy()
+    nan[1, 2] = np.nan
+    with pytest.raises(panda.PandaError) as e:
+        panda.PandaContext(nan, P0, C0)
+    assert e.value.code == -4
+    with pytest.raises(panda.PandaError) as e:
+        panda.PandaContext(np.ones_like(W0), P0, C0)
+    assert e.value.code == -6
+    with panda.PandaContext(W0, P0, C0) as ctx:
+        with pytest.raises(panda.PandaError) as e:
+            ctx.step(1.5)
+        assert e.value.code == -1
+        with pytest.raises(panda.PandaError) as e:
+            ctx.run(0.1, -1.0, 3)
+        assert e.value.code == -1
+        conv, n, h = ctx.run(0.1, 0.0, 2)
+        assert not conv and n == 2
+
+
+def test_allocation_cap_gives_enomem(panda, monkeypatch):
+    W0, P0, C0 = gh.inputs("small64x256")
+    monkeypatch.setenv("PANDA_ALLOC_LIMIT_BYTES", "100000")
+    with pytest.raises(panda.PandaError) as e:
+        panda.PandaContext(W0, P0, C0)
+    assert e.value.code == -2
+    monkeypatch.delenv("PANDA_ALLOC_LIMIT_BYTES")
+    with panda.PandaContext(W0, P0, C0) as ctx:
+        ctx.step(0.1)

@@ -27,13 +27,13 @@ MUTANTS = {
     "p_from_old_W": ("oracle_p_rows(T, G, Wn, P, alpha, T, idx, Pn, Psim)",
                      "oracle_p_rows(T, G, W, P, alpha, T, idx, Pn, Psim)"),
     "c_from_old_W": ("int rc = oracle_c_rows(T, G, Wn, C,", "int rc = oracle_c_rows(T, G, W, C,"),
-    "p_half_alpha": ("v = (1.0 - alpha) * P[i * T + m] + alpha * s;",
-                     "v = (1.0 - alpha) * P[i * T + m] + alpha / 2.0 * s;"),
-    "c_no_damping": ("v = (1.0 - alpha) * C[k * G + j] + alpha * s;", "v = C[k * G + j] + alpha * s;"),
+    "eq5_half_alpha": ("return (1.0 - alpha) * old + alpha * s;", "return (1.0 - alpha) * old + alpha / 2.0 * s;"),
+    "eq5_no_damping": ("return (1.0 - alpha) * old + alpha * s;", "return old + alpha * s;"),
+    "p_from_C_row_old": ("v = oracle_eq5_entry(P[i * T + m], alpha,", "v = oracle_eq5_entry(P[m * T + m], alpha,"),
     "diag_multipliers_swapped": ("diag_update(T, (double)G, Pn, P, Psim", "diag_update(T, (double)T, Pn, P, Psim"),
     "diag_t_off_by_one": ("exp(2.0 * alpha * (double)t)", "exp(2.0 * alpha * (double)(t - 1))"),
-    "diag_no_damping_old": ("Xn[(long)i * n + i] = (1.0 - alpha) * Xold[(long)i * n + i] +",
-                            "Xn[(long)i * n + i] = Xold[(long)i * n + i] +"),
+    "diag_no_damping_old": ("return (1.0 - alpha) * old + gain * mult * sigma * growth;",
+                            "return old + gain * mult * sigma * growth;"),
     "diag_sample_std": ("return sqrt(ss / (double)(n - 1));", "return sqrt(ss / (double)(n > 2 ? n - 2 : 1));"),
     "diag_includes_diagonal": ("    double mean = s / (double)(n - 1);",
                                "    s += X[(long)i * n + i];\n    double mean = s / (double)(n - 1);"),
