@@ -95,8 +95,8 @@ struct KernelEvents {
     int n;  // events recorded so far
     void mark(cudaStream_t s)
     {
-        if (ev)
-            cudaEventRecord(ev[n++], s);
+        if (ev)  // external: inside a graph capture this becomes an event-record node
+            cudaEventRecordWithFlags(ev[n++], s, cudaEventRecordExternal);
     }
 };
 
