@@ -384,8 +384,8 @@ __global__ void k_fin(Dev d)
     const double alpha = (double)ctl->alpha;
     const int t = ctl->iters + 1;
     const double growth = d.e2tab[t < HIST_CAP ? t : HIST_CAP];
-    double sigma = 0.0;
-    if (n > 1) {
+    double sigma = 0.0;  // population std of the n - 1 off-diagonal entries (0 for one entry)
+    if (n > 2) {
         const double m = s1 / (double)(n - 1);
         const double var = s2 / (double)(n - 1) - m * m;
         sigma = var > 0.0 ? sqrt(var) : 0.0;

@@ -43,7 +43,9 @@ def test_small_network_full_trajectory(orc, prec):
         o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, o["iters"])
         g = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, o["iters"])
     assert g["iters"] == o["iters"] and g["converged"] == o["converged"]
-    np.testing.assert_allclose(g["hist"], o["hist"], rtol=1e-4 if prec else 1e-5, atol=1e-9)
+    # h is a mean of |dW|; its error is bounded by the mean error of W and W'
+    np.testing.assert_allclose(g["hist"], o["hist"], rtol=1e-3 if prec else 1e-4,
+                               atol=1e-6 if prec else 1e-7)
     gh.assert_parity(g, o, prec, "small")
 
 
