@@ -52,6 +52,8 @@ WORKLOADS = {
     "human1000x17000": Workload("human1000x17000", 1000, 17000, 200, 20, 0.05, 0.01, BASE_SEED + 1),
     # large network: 1600 TFs x 30000 genes, 300 samples from 30 factors.
     "large1600x30000": Workload("large1600x30000", 1600, 30000, 300, 30, 0.05, 0.01, BASE_SEED + 4),
+    # profiling case: same TF count, C (268 MB) still larger than L2, a few GB on the device.
+    "prof1000x8192": Workload("prof1000x8192", 1000, 8192, 100, 10, 0.05, 0.01, BASE_SEED + 8),
     # mid-size parity case spanning many tiles with ragged edges.
     "mid250x2100": Workload("mid250x2100", 250, 2100, 100, 10, 0.05, 0.02, BASE_SEED + 7),
 }
