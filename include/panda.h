@@ -163,12 +163,46 @@ int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, do
 /* The context's stream as a cudaStream_t. */
 void *panda_stream(const panda_ctx *ctx);
 
-/* Message of the last error on ctx (or of the last failed create when ctx is
- * NULL); never NULL. */
+/* Message of the last error on ctx (or, when ctx is NULL, of the last failed
+ * create or panda_step_static on this thread); never NULL. */
 const char *panda_last_error(const panda_ctx *ctx);
 
 /* Free everything the context owns.  NULL is ignored. */
 void panda_destroy(panda_ctx *ctx);
+
+/* ---- allocation-free single iteration ---------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that are not allowed to allocate device memory: code running inside a host
+ * framework that hands out all device memory from its own pool or budget,
+ * plug-ins that must not call cudaMalloc once the process is running, or
+ * loops where cudaMalloc's implicit device synchronisation is not
+ * acceptable.  panda_step_static runs one message-passing iteration (the same
+ * FP32 kernels as panda_step, so the same results) directly on the caller's
+ * device networks and calls no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *
+ * dW (T x G), dP (T x T) and dC (G x G) are dense row-major FP32 device
+ * buffers, diagonals included, owned by the caller and updated in place.
+ * They are used as given: no Z-score is applied (normalise them first, or
+ * take them from panda_get).  dP and dC must be exactly symmetric
+ * (PANDA_EASYM) and finite (PANDA_ENONFINITE).  alpha in [0, 1]; t >= 1 is
+ * the 1-based iteration index used in the e^{2 alpha t} factor of Eq. 6;
+ * diag is a panda_diag rule.  *h_out (may be NULL) receives h.  The call
+ * runs on `stream` (a cudaStream_t, NULL = legacy default stream) and blocks
+ * until the iteration is done.
+ *
+ * Working memory is one file-scope device array of about 7.4 MB, sized for
+ * T, G <= PANDA_STATIC_MAX_NODES; larger shapes are rejected with
+ * PANDA_EINVAL before any GPU work.  Every GPU that loads the library holds
+ * the array until the process exits.  The first call on each device looks up
+ * the array's device address (with that device current); make that first
+ * call before any stream capture.  All calls share the array and clear it at
+ * their start, so calls that overlap on the GPU (for example on two streams)
+ * race and must be serialised by the caller.  Errors are reported by the
+ * return code and panda_last_error(NULL). */
+#define PANDA_STATIC_MAX_NODES 512
+int panda_step_static(int T, int G, float *dW, float *dP, float *dC, float alpha, int t, int diag,
+                      double *h_out, void *stream);
 
 #ifdef __cplusplus
 }

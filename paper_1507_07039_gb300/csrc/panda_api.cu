@@ -489,6 +489,10 @@ int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P
 
 }  // namespace
 
+namespace panda {
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+}  // namespace panda
+
 extern "C" {
 
 int panda_precision_supported(int prec)

@@ -64,6 +64,7 @@ def _load() -> ctypes.CDLL:
         "panda_kernel_stats": (i, [vp, i, ctypes.c_char_p, i, pd, ctypes.POINTER(ll)]),
         "panda_last_error": (ctypes.c_char_p, [vp]),
         "panda_precision_supported": (i, [i]),
+        "panda_step_static": (i, [i, i, vp, vp, vp, f, i, i, pd, vp]),
         "panda_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -235,6 +236,20 @@ def panda_kernel_stats(ctx, i: int):
     ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
     _check(lib.panda_kernel_stats(ctx, int(i), name, 64, ctypes.byref(ms), ctypes.byref(n)), ctx)
     return name.value.decode(), ms.value, n.value
+
+
+PANDA_STATIC_MAX_NODES = 512
+
+
+def panda_step_static(T, G, dW, dP, dC, alpha: float, t: int, diag: int = PANDA_DIAG_D1, stream=None) -> float:
+    """One iteration in place on caller-owned device networks (torch CUDA
+    tensors or raw pointers) with no device allocation; returns h."""
+    def ptr(x):
+        return ctypes.c_void_p(x if isinstance(x, int) else x.data_ptr())
+    h = ctypes.c_double(0.0)
+    _check(lib.panda_step_static(int(T), int(G), ptr(dW), ptr(dP), ptr(dC), float(alpha), int(t),
+                                 int(diag), ctypes.byref(h), ctypes.c_void_p(stream or 0)))
+    return h.value
 
 
 def panda_last_error(ctx=None) -> str:
