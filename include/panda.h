@@ -160,6 +160,13 @@ int panda_kernel_count(const panda_ctx *ctx);
 int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, double *total_ms,
                        long long *launches);
 
+/* Self-test of the tensor-core pipeline (no paper counterpart): D = A . B^T
+ * computed by the same TMA + tcgen05 + TMEM machinery the BF16X3 iteration
+ * uses.  A is M x K, B is N x K, D is M x N, all row-major FP32 host buffers;
+ * each operand is split into BF16 hi + lo and terms = 3 sums hi*hi + hi*lo +
+ * lo*hi, terms = 1 uses hi*hi only.  PANDA_EUNSUPPORTED off sm_103. */
+int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms);
+
 /* The context's stream as a cudaStream_t. */
 void *panda_stream(const panda_ctx *ctx);
 

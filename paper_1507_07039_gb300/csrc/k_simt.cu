@@ -441,6 +441,12 @@ __global__ void k_tail(Dev d)
 const char *const SIMT_KERNEL_NAMES[SIMT_KERNELS] = {"k_rn", "k_phase1", "k_reduce_wnorms",
                                                      "k_phase2", "k_fin", "k_tail"};
 
+cudaError_t launch_reduce_wnorms(const Dev &d, cudaStream_t s)
+{
+    k_reduce_wnorms<<<ceil_div(d.T + d.G, 256), 256, 0, s>>>(d);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fin_tail(const Dev &d, cudaStream_t s, KernelEvents &ke)
 {
     k_fin<<<ceil_div(d.T + d.G, 256), 256, 0, s>>>(d);

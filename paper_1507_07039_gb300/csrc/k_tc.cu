@@ -1,11 +1,676 @@
-// Tensor-core (tcgen05) path: placeholder until the BF16X3 kernels land.
+// BF16X3 tensor-core path of one PANDA iteration (sm_103a, tcgen05 + TMA).
+//
+//   k_tc_phase1   per 128 x BN1 tile of W': two TMEM accumulators,
+//                   R-num = P_off . W   (K = TFs;   A = P_off rows, B = W^T rows)
+//                   A-num = W . C_off   (K = genes; A = W rows,     B = C_off rows)
+//                 then the fused epilogue of Eqs. 1-3 and 2: diagonal terms,
+//                 Tanimoto, damped W update, h and norm partials, and the
+//                 FP32 W' plus its split copies in both orientations.
+//   k_reduce_wnorms  (shared with the FP32 path)
+//   k_tc_phase2   upper-triangle 128 x 128 tiles of W'.W'^T (P, K = genes) and
+//                 W'^T.W' (C, K = TFs) in one launch, P tiles first, with the
+//                 Eq. 5 epilogue: Tanimoto, damped update, mirrored FP32 and
+//                 split stores, row partial sums for Eq. 6.
+//   k_fin, k_tail (shared): Eq. 6 diagonals, norms, h, stop test.
+//
+// C and P are symmetric, so "C_off rows" and "P_off rows" are the K-major
+// layouts the B and A operands need.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "panda_internal.cuh"
+#include "tc_common.cuh"
 
 namespace panda {
 
-const char *const TC_KERNEL_NAMES[TC_KERNELS] = {"", "", "", "", "", ""};
-bool tc_supported() { return false; }
-cudaError_t tc_prepare(Dev &, cudaStream_t) { return cudaErrorNotSupported; }
-cudaError_t launch_iteration_tc(const Dev &, int, cudaStream_t, KernelEvents &) { return cudaErrorNotSupported; }
+const char *const TC_KERNEL_NAMES[TC_KERNELS] = {"k_tc_phase1", "k_reduce_wnorms", "k_tc_phase2",
+                                                 "k_fin", "k_tail"};
+
+namespace {
+
+using namespace tc;
+
+constexpr int BN1 = 256;     // phase-1 tile width (genes)
+constexpr int ST1 = 2;       // phase-1 pipeline stages (96 KB each)
+constexpr int ST2 = 3;       // phase-2 pipeline stages (64 KB each)
+
+struct TcMaps {
+    CUtensorMap Ph, Pl;              // P_off split   [Tp][Tp]  box 64 x 128
+    CUtensorMap Wh[2], Wl[2];        // W split       [Tp][Gp]  box 64 x 128
+    CUtensorMap Wth1[2], Wtl1[2];    // W^T split     [Gp][Tp]  box 64 x BN1
+    CUtensorMap Wth2[2], Wtl2[2];    // W^T split     [Gp][Tp]  box 64 x 128
+    CUtensorMap Ch1, Cl1;            // C_off split   [Gp][Gp]  box 64 x BN1
+};
+
+__device__ __forceinline__ uint8_t *align1024(uint8_t *p)
+{
+    return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+__device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(x);
+    lo = __float2bfloat16_rn(x - __bfloat162float(hi));  // x - hi is exact in FP32
+}
+
+// hi / lo of a whole array (padding stays zero because x is zero there)
+__global__ void k_split(const float *__restrict__ X, size_t n, __nv_bfloat16 *__restrict__ H,
+                        __nv_bfloat16 *__restrict__ L)
+{
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        split_bf16(X[q], H[q], L[q]);
+}
+
+__device__ __forceinline__ void tri_decode(int u, int nb, int &bm, int &bn)
+{
+    int r = 0;
+    while (u >= nb - r) {
+        u -= nb - r;
+        ++r;
+    }
+    bm = r;
+    bn = r + u;
+}
+
+template <int STAGES>
+__device__ __forceinline__ void init_sync(Sync<STAGES> &sy)
+{
+    for (int s = 0; s < STAGES; ++s) {
+        mbar_init(&sy.full[s], 1);
+        mbar_init(&sy.empty[s], 1);
+    }
+    mbar_init(&sy.accum, 1);
+    sy.abort = 0;
+    sy.issued = 0;
+    sy.consumed = 0;
+    fence_mbar_init();
+}
+
+// store 32 consecutive floats (16-byte aligned destination)
+__device__ __forceinline__ void st32(float *dst, const float (&v)[32])
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+__device__ __forceinline__ void ld32(const float *src, float (&v)[32])
+{
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float4 x = reinterpret_cast<const float4 *>(src)[q];
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+}
+
+// 32 consecutive BF16 (64 bytes, 16-byte aligned destination)
+__device__ __forceinline__ void st32_bf16(__nv_bfloat16 *dst, const __nv_bfloat16 (&v)[32])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint4 u;
+        u.x = (uint32_t)__bfloat16_as_ushort(v[8 * q + 0]) | ((uint32_t)__bfloat16_as_ushort(v[8 * q + 1]) << 16);
+        u.y = (uint32_t)__bfloat16_as_ushort(v[8 * q + 2]) | ((uint32_t)__bfloat16_as_ushort(v[8 * q + 3]) << 16);
+        u.z = (uint32_t)__bfloat16_as_ushort(v[8 * q + 4]) | ((uint32_t)__bfloat16_as_ushort(v[8 * q + 5]) << 16);
+        u.w = (uint32_t)__bfloat16_as_ushort(v[8 * q + 6]) | ((uint32_t)__bfloat16_as_ushort(v[8 * q + 7]) << 16);
+        reinterpret_cast<uint4 *>(dst)[q] = u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Self-test: D (Mp x Np) = A . B^T from split operands, one 128 x 128 tile per CTA
+// ---------------------------------------------------------------------------
+struct GemmMaps {
+    CUtensorMap Ah, Al, Bh, Bl;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_tc_selftest(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl)
+{
+    constexpr int BN = 128, STAGES = 3;
+    constexpr uint32_t B_BYTES = BN * BK * 2, STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *stages = align1024(smem_raw);
+    Sync<STAGES> &sy = *reinterpret_cast<Sync<STAGES> *>(stages + STAGES * STAGE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, nk = Kp / BK;
+    if (threadIdx.x == 0)
+        init_sync(sy);
+    if (warp == 1)
+        tmem_alloc(&sy.tmem, BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) {
+        if (lane == 0)
+            run_producer<STAGES>(sy, stages, STAGE, nk, ctl, [&](int kb, uint8_t *st, uint64_t *bar) {
+                tma_load_2d(st, &maps.Ah, bar, kb * BK, m0);
+                tma_load_2d(st + A_BYTES, &maps.Al, bar, kb * BK, m0);
+                tma_load_2d(st + 2 * A_BYTES, &maps.Bh, bar, kb * BK, n0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.Bl, bar, kb * BK, n0);
+            });
+    } else if (warp == 1) {
+        if (lane == 0)
+            run_mma<STAGES, BN>(sy, stages, STAGE, nk, ctl, [](int) { return 0u; }, [](int kb) { return kb == 0; });
+    } else {
+        const int wq = warp & 3;
+        const bool ok = wait_bounded(&sy.accum, 0, &sy.abort, ctl);
+        tc_fence_after();
+        if (ok && !*(volatile int *)&sy.abort) {
+            const int r = m0 + wq * 32 + lane;
+            const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                float v[32];
+                tmem_ld32(trow + c * 32, v);
+                st32(D + (size_t)r * Np + n0 + c * 32, v);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        drain(sy, ctl);
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(sy.tmem, BN);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Phase 1 (grid: x = T tile of 128, y = G tile of BN1)
+// ---------------------------------------------------------------------------
+constexpr size_t phase1_smem()
+{
+    return 1024 + (size_t)ST1 * (2 * A_BYTES + 2 * BN1 * BK * 2) + sizeof(Sync<ST1>) + 16 +
+           4 * BN1 * sizeof(float) + 4 * sizeof(double);
+}
+
+__global__ void __launch_bounds__(THREADS, 1) k_tc_phase1(const __grid_constant__ TcMaps maps, Dev d, int cur)
+{
+    Ctl *ctl = d.ctl;
+    if (!ctl->active)
+        return;
+    constexpr int BN = BN1, STAGES = ST1;
+    constexpr uint32_t B_BYTES = BN * BK * 2, STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *stages = align1024(smem_raw);
+    Sync<STAGES> &sy = *reinterpret_cast<Sync<STAGES> *>(stages + STAGES * STAGE);
+    float *colred = reinterpret_cast<float *>(stages + STAGES * STAGE + ((sizeof(Sync<STAGES>) + 15) & ~15));
+    double *hred = reinterpret_cast<double *>(colred + 4 * BN);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nR = d.Tp / BK, nk = nR + d.Gp / BK;
+
+    if (threadIdx.x == 0)
+        init_sync(sy);
+    if (warp == 1)
+        tmem_alloc(&sy.tmem, 2 * BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (warp == 0) {
+        if (lane == 0)
+            run_producer<STAGES>(sy, stages, STAGE, nk, ctl, [&](int kb, uint8_t *st, uint64_t *bar) {
+                if (kb < nR) {  // responsibility: P_off rows x W^T rows, K over TFs
+                    const int k = kb * BK;
+                    tma_load_2d(st, &maps.Ph, bar, k, m0);
+                    tma_load_2d(st + A_BYTES, &maps.Pl, bar, k, m0);
+                    tma_load_2d(st + 2 * A_BYTES, &maps.Wth1[cur], bar, k, n0);
+                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.Wtl1[cur], bar, k, n0);
+                } else {        // availability: W rows x C_off rows, K over genes
+                    const int k = (kb - nR) * BK;
+                    tma_load_2d(st, &maps.Wh[cur], bar, k, m0);
+                    tma_load_2d(st + A_BYTES, &maps.Wl[cur], bar, k, m0);
+                    tma_load_2d(st + 2 * A_BYTES, &maps.Ch1, bar, k, n0);
+                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.Cl1, bar, k, n0);
+                }
+            });
+    } else if (warp == 1) {
+        if (lane == 0)
+            run_mma<STAGES, BN>(
+                sy, stages, STAGE, nk, ctl, [&](int kb) { return kb < nR ? 0u : (uint32_t)BN; },
+                [&](int kb) { return kb == 0 || kb == nR; });
+    } else {
+        // ---- epilogue: one row of the tile per thread ----
+        const int wq = warp & 3, ew = warp - 2;
+        const int i = m0 + wq * 32 + lane;
+        const bool ok = wait_bounded(&sy.accum, 0, &sy.abort, ctl);
+        tc_fence_after();
+        const bool live = ok && !*(volatile int *)&sy.abort;
+        float rowsq = 0.0f, hsum = 0.0f;
+        if (live) {
+            const bool ri = i < d.T;
+            const float pdi = ri ? d.pdf[i] : 0.0f, rsp = ri ? d.rsqP[i] : 0.0f, rsw = ri ? d.rsqW[i] : 0.0f;
+            const float a = ctl->alpha, keep = 1.0f - a, half = 0.5f * a;
+            const int nx = cur ^ 1;
+            const float *W = d.W[cur];
+            float *Wn = d.W[nx];
+            __nv_bfloat16 *Wh = d.Wh[nx], *Wl = d.Wl[nx], *Wth = d.Wth[nx], *Wtl = d.Wtl[nx];
+            const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                const int j0 = n0 + c * 32;
+                if (j0 >= d.Gp) {  // beyond the padded width (warp-uniform)
+                    colred[ew * BN + c * 32 + lane] = 0.0f;
+                    continue;
+                }
+                float rr[32], aa[32], w[32], wn[32];
+                tmem_ld32(trow + c * 32, rr);
+                tmem_ld32(trow + BN + c * 32, aa);
+                const size_t o = (size_t)i * d.Gp + j0;
+                ld32(W + o, w);
+                __nv_bfloat16 hv[32], lv[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int j = j0 + q;
+                    wn[q] = 0.0f;
+                    if (ri && j < d.G) {
+                        const float rnum = rr[q] + pdi * w[q];       // P_i. . W_.j
+                        const float anum = aa[q] + w[q] * d.cdf[j];  // W_i. . C_.j
+                        const float R = tanimoto_f(rnum, rsp, d.csqW[j]);
+                        const float A = tanimoto_f(anum, rsw, d.csqC[j]);
+                        wn[q] = keep * w[q] + half * (A + R);
+                        hsum += fabsf(wn[q] - w[q]);
+                        rowsq += wn[q] * wn[q];
+                    }
+                    split_bf16(wn[q], hv[q], lv[q]);
+                }
+                st32(Wn + o, wn);
+                st32_bf16(Wh + o, hv);
+                st32_bf16(Wl + o, lv);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {  // transposed copies: lanes write consecutive TFs
+                    Wth[(size_t)(j0 + q) * d.Tp + i] = hv[q];
+                    Wtl[(size_t)(j0 + q) * d.Tp + i] = lv[q];
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    wn[q] *= wn[q];
+                colred[ew * BN + c * 32 + lane] = lane_transpose_sum(wn);
+            }
+        }
+        epi_bar();
+        const int t = threadIdx.x - 64;  // 0..127
+        if (live) {
+            for (int col = t; col < BN; col += 128) {
+                const int j = n0 + col;
+                if (j < d.Gp)
+                    d.wcol_part[(size_t)blockIdx.x * d.Gp + j] =
+                        ((colred[col] + colred[BN + col]) + colred[2 * BN + col]) + colred[3 * BN + col];
+            }
+            d.wrow_part[(size_t)blockIdx.y * d.Tp + i] = rowsq;
+        }
+        double hv = (double)hsum;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1)
+            hv += __shfl_xor_sync(0xffffffffu, hv, off);
+        if (lane == 0)
+            hred[ew] = hv;
+        epi_bar();
+        if (t == 0 && live)
+            d.hpart[(size_t)blockIdx.y * d.nbT + blockIdx.x] = ((hred[0] + hred[1]) + hred[2]) + hred[3];
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        drain(sy, ctl);
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(sy.tmem, 2 * BN);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Phase 2 (grid: upper-triangle tiles of P, then of C)
+// ---------------------------------------------------------------------------
+constexpr size_t phase2_smem()
+{
+    return 1024 + (size_t)ST2 * (4 * A_BYTES) + sizeof(Sync<ST2>) + 16 + 3 * 4 * 128 * sizeof(float) +
+           3 * 128 * sizeof(float);
+}
+
+template <bool SIM_SIGMA>
+__global__ void __launch_bounds__(THREADS, 1) k_tc_phase2(const __grid_constant__ TcMaps maps, Dev d, int cur)
+{
+    Ctl *ctl = d.ctl;
+    if (!ctl->active)
+        return;
+    constexpr int BN = 128, STAGES = ST2;
+    constexpr uint32_t B_BYTES = BN * BK * 2, STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *stages = align1024(smem_raw);
+    Sync<STAGES> &sy = *reinterpret_cast<Sync<STAGES> *>(stages + STAGES * STAGE);
+    float *colred = reinterpret_cast<float *>(stages + STAGES * STAGE + ((sizeof(Sync<STAGES>) + 15) & ~15));
+    float *rowred = colred + 3 * 4 * BN;  // [3][128]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nP = d.nbT * (d.nbT + 1) / 2;
+    const bool isP = (int)blockIdx.x < nP;
+    int bm, bn;
+    tri_decode(isP ? (int)blockIdx.x : (int)blockIdx.x - nP, isP ? d.nbT : d.nbG, bm, bn);
+    const int m0 = bm * BM, n0 = bn * BN;
+    const int nk = (isP ? d.Gp : d.Tp) / BK;
+    const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Wth2[cur];
+    const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl2[cur];
+
+    if (threadIdx.x == 0)
+        init_sync(sy);
+    if (warp == 1)
+        tmem_alloc(&sy.tmem, BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+
+    if (warp == 0) {
+        if (lane == 0)
+            run_producer<STAGES>(sy, stages, STAGE, nk, ctl, [&](int kb, uint8_t *st, uint64_t *bar) {
+                const int k = kb * BK;
+                tma_load_2d(st, mh, bar, k, m0);
+                tma_load_2d(st + A_BYTES, ml, bar, k, m0);
+                tma_load_2d(st + 2 * A_BYTES, mh, bar, k, n0);
+                tma_load_2d(st + 2 * A_BYTES + B_BYTES, ml, bar, k, n0);
+            });
+    } else if (warp == 1) {
+        if (lane == 0)
+            run_mma<STAGES, BN>(sy, stages, STAGE, nk, ctl, [](int) { return 0u; }, [](int kb) { return kb == 0; });
+    } else {
+        const int wq = warp & 3, ew = warp - 2;
+        const int r = wq * 32 + lane;
+        const int n = isP ? d.T : d.G, ld = isP ? d.Tp : d.Gp;
+        const float *nrm = isP ? d.rsqW : d.csqW;
+        float *X = isP ? d.Poff : d.Coff;
+        __nv_bfloat16 *Xh = isP ? d.Ph : d.Ch, *Xl = isP ? d.Pl : d.Cl;
+        const int k = m0 + r;
+        const bool ok = wait_bounded(&sy.accum, 0, &sy.abort, ctl);
+        tc_fence_after();
+        const bool live = ok && !*(volatile int *)&sy.abort;
+        float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
+        if (live) {
+            const float a = ctl->alpha, keep = 1.0f - a;
+            const float nk_ = k < n ? nrm[k] : 0.0f;
+            const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                const int j0 = n0 + c * 32;
+                float acc[32], old[32];
+                tmem_ld32(trow + c * 32, acc);
+                ld32(X + (size_t)k * ld + j0, old);
+                float c1[32], c2[32], cv[32];
+                bool all = true;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int j = j0 + q;
+                    const bool valid = k < j && j < n;
+                    all = all && valid;
+                    c1[q] = c2[q] = cv[q] = 0.0f;
+                    if (valid) {
+                        const float s = tanimoto_f(acc[q], nk_, nrm[j]);
+                        const float v = keep * old[q] + a * s;
+                        const float x = SIM_SIGMA ? s : v;
+                        r1 += x; r2 += x * x; rv += v * v;
+                        c1[q] = x; c2[q] = x * x; cv[q] = v * v;
+                        old[q] = v;  // now the value to store
+                    }
+                    acc[q] = valid ? 1.0f : 0.0f;  // validity mask from here on
+                }
+                __nv_bfloat16 hv[32], lv[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    split_bf16(old[q], hv[q], lv[q]);
+                const size_t o = (size_t)k * ld + j0;
+                if (all) {
+                    st32(X + o, old);
+                    st32_bf16(Xh + o, hv);
+                    st32_bf16(Xl + o, lv);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (acc[q] != 0.0f) {
+                            X[o + q] = old[q];
+                            Xh[o + q] = hv[q];
+                            Xl[o + q] = lv[q];
+                        }
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q)  // mirrored entries: lanes write consecutive rows
+                    if (acc[q] != 0.0f) {
+                        const size_t mo = (size_t)(j0 + q) * ld + k;
+                        X[mo] = old[q];
+                        Xh[mo] = hv[q];
+                        Xl[mo] = lv[q];
+                    }
+                colred[(0 * 4 + ew) * BN + c * 32 + lane] = lane_transpose_sum(c1);
+                colred[(1 * 4 + ew) * BN + c * 32 + lane] = lane_transpose_sum(c2);
+                colred[(2 * 4 + ew) * BN + c * 32 + lane] = lane_transpose_sum(cv);
+            }
+        }
+        rowred[0 * BN + r] = r1;
+        rowred[1 * BN + r] = r2;
+        rowred[2 * BN + r] = rv;
+        epi_bar();
+        const int t = threadIdx.x - 64;
+        if (live) {
+            float *S[3] = {isP ? d.ps_sum : d.cs_sum, isP ? d.ps_sq : d.cs_sq, isP ? d.ps_vsq : d.cs_vsq};
+#pragma unroll
+            for (int w = 0; w < 3; ++w) {
+                const float cs = ((colred[(w * 4 + 0) * BN + t] + colred[(w * 4 + 1) * BN + t]) +
+                                  colred[(w * 4 + 2) * BN + t]) + colred[(w * 4 + 3) * BN + t];
+                const float rs = rowred[w * BN + t];
+                if (bm == bn) {
+                    S[w][(size_t)bm * ld + m0 + t] = rs + cs;
+                } else {
+                    S[w][(size_t)bn * ld + m0 + t] = rs;  // rows of this tile, slot of its column block
+                    S[w][(size_t)bm * ld + n0 + t] = cs;  // mirrored rows, slot of its row block
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        drain(sy, ctl);
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(sy.tmem, BN);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Row-major BF16 matrix rows x cols (cols = K, contiguous), box 64 x box_rows,
+// 128-byte swizzle.
+cudaError_t make_map(CUtensorMap *m, const void *base, int rows, int cols, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t set_smem_limits()
+{
+    static bool done = false;
+    if (done)
+        return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_tc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phase1_smem())))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_tc_phase2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)phase2_smem())))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_tc_phase2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)phase2_smem())))
+        return e;
+    constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
+    if ((e = cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem)))
+        return e;
+    done = true;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+bool tc_supported()
+{
+    int dev = 0, major = 0, minor = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return false;
+    if (cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess)
+        return false;
+    return major == 10 && minor == 3 && encode_fn() != nullptr;
+}
+
+cudaError_t tc_prepare(Dev &d, cudaStream_t s)
+{
+    cudaError_t e = set_smem_limits();
+    if (e)
+        return e;
+    const size_t TG = (size_t)d.Tp * d.Gp;
+    // split copies of the current state (both W buffers get their maps; buffer 0 holds W now)
+    for (int b = 0; b < 2; ++b) {
+        k_split<<<1024, 256, 0, s>>>(d.W[b], TG, d.Wh[b], d.Wl[b]);
+        k_split<<<1024, 256, 0, s>>>(d.Wt[b], TG, d.Wth[b], d.Wtl[b]);
+    }
+    k_split<<<1024, 256, 0, s>>>(d.Poff, (size_t)d.Tp * d.Tp, d.Ph, d.Pl);
+    k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, d.Cl);
+    if ((e = cudaGetLastError()))
+        return e;
+    if (!d.tc_host) {
+        TcMaps *m = new TcMaps;
+        std::memset(m, 0, sizeof *m);
+        if ((e = make_map(&m->Ph, d.Ph, d.Tp, d.Tp, 128)) || (e = make_map(&m->Pl, d.Pl, d.Tp, d.Tp, 128)) ||
+            (e = make_map(&m->Ch1, d.Ch, d.Gp, d.Gp, BN1)) || (e = make_map(&m->Cl1, d.Cl, d.Gp, d.Gp, BN1))) {
+            delete m;
+            return e;
+        }
+        for (int b = 0; b < 2; ++b)
+            if ((e = make_map(&m->Wh[b], d.Wh[b], d.Tp, d.Gp, 128)) ||
+                (e = make_map(&m->Wl[b], d.Wl[b], d.Tp, d.Gp, 128)) ||
+                (e = make_map(&m->Wth1[b], d.Wth[b], d.Gp, d.Tp, BN1)) ||
+                (e = make_map(&m->Wtl1[b], d.Wtl[b], d.Gp, d.Tp, BN1)) ||
+                (e = make_map(&m->Wth2[b], d.Wth[b], d.Gp, d.Tp, 128)) ||
+                (e = make_map(&m->Wtl2[b], d.Wtl[b], d.Gp, d.Tp, 128))) {
+                delete m;
+                return e;
+            }
+        d.tc_host = m;
+    }
+    return cudaSuccess;
+}
+
+void tc_release(Dev &d)
+{
+    delete static_cast<TcMaps *>(d.tc_host);
+    d.tc_host = nullptr;
+}
+
+cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke)
+{
+    const TcMaps &m = *static_cast<const TcMaps *>(d.tc_host);
+    ke.mark(s);
+    dim3 g1(d.nbT, ceil_div(d.Gp, BN1));
+    k_tc_phase1<<<g1, THREADS, phase1_smem(), s>>>(m, d, cur);
+    ke.mark(s);
+    cudaError_t e = launch_reduce_wnorms(d, s);
+    if (e)
+        return e;
+    ke.mark(s);
+    const int tiles = d.nbT * (d.nbT + 1) / 2 + d.nbG * (d.nbG + 1) / 2;
+    if (d.diag == 2)
+        k_tc_phase2<true><<<tiles, THREADS, phase2_smem(), s>>>(m, d, cur ^ 1);
+    else
+        k_tc_phase2<false><<<tiles, THREADS, phase2_smem(), s>>>(m, d, cur ^ 1);
+    ke.mark(s);
+    return launch_fin_tail(d, s, ke);
+}
+
+// D = A . B^T on the tensor-core pipeline (self-test support)
+cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms,
+                             int *status)
+{
+    cudaError_t e = set_smem_limits();
+    if (e)
+        return e;
+    const int Mp = round_up(M, 128), Np = round_up(N, 128), Kp = round_up(K, 64);
+    float *dA = nullptr, *dB = nullptr, *dD = nullptr;
+    __nv_bfloat16 *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
+    Ctl *ctl = nullptr;
+    GemmMaps maps;
+    auto cleanup = [&]() {
+        cudaFree(dA); cudaFree(dB); cudaFree(dD); cudaFree(Ah); cudaFree(Al); cudaFree(Bh); cudaFree(Bl);
+        cudaFree(ctl);
+    };
+#define TRY(x)            \
+    if ((e = (x))) {      \
+        cleanup();        \
+        return e;         \
+    }
+    TRY(cudaMalloc(&dA, (size_t)Mp * Kp * 4));
+    TRY(cudaMalloc(&dB, (size_t)Np * Kp * 4));
+    TRY(cudaMalloc(&dD, (size_t)Mp * Np * 4));
+    TRY(cudaMalloc(&Ah, (size_t)Mp * Kp * 2));
+    TRY(cudaMalloc(&Al, (size_t)Mp * Kp * 2));
+    TRY(cudaMalloc(&Bh, (size_t)Np * Kp * 2));
+    TRY(cudaMalloc(&Bl, (size_t)Np * Kp * 2));
+    TRY(cudaMalloc(&ctl, sizeof(Ctl)));
+    TRY(cudaMemset(ctl, 0, sizeof(Ctl)));
+    TRY(cudaMemset(dA, 0, (size_t)Mp * Kp * 4));
+    TRY(cudaMemset(dB, 0, (size_t)Np * Kp * 4));
+    TRY(cudaMemcpy2D(dA, (size_t)Kp * 4, A, (size_t)K * 4, (size_t)K * 4, M, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy2D(dB, (size_t)Kp * 4, B, (size_t)K * 4, (size_t)K * 4, N, cudaMemcpyHostToDevice));
+    k_split<<<256, 256>>>(dA, (size_t)Mp * Kp, Ah, Al);
+    k_split<<<256, 256>>>(dB, (size_t)Np * Kp, Bh, Bl);
+    TRY(cudaGetLastError());
+    if (terms == 1) {  // hi only: zero the lo halves
+        TRY(cudaMemset(Al, 0, (size_t)Mp * Kp * 2));
+        TRY(cudaMemset(Bl, 0, (size_t)Np * Kp * 2));
+    }
+    TRY(make_map(&maps.Ah, Ah, Mp, Kp, 128));
+    TRY(make_map(&maps.Al, Al, Mp, Kp, 128));
+    TRY(make_map(&maps.Bh, Bh, Np, Kp, 128));
+    TRY(make_map(&maps.Bl, Bl, Np, Kp, 128));
+    constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
+    k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl);
+    TRY(cudaGetLastError());
+    TRY(cudaDeviceSynchronize());
+    Ctl h;
+    TRY(cudaMemcpy(&h, ctl, sizeof h, cudaMemcpyDeviceToHost));
+    *status = h.status;
+    TRY(cudaMemcpy2D(D, (size_t)N * 4, dD, (size_t)Np * 4, (size_t)N * 4, M, cudaMemcpyDeviceToHost));
+    cleanup();
+#undef TRY
+    return cudaSuccess;
+}
 
 }  // namespace panda

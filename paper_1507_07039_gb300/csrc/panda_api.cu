@@ -152,13 +152,6 @@ int plan_memory(panda_ctx *c)
         DALLOC(d.Pl, Tp * Tp);
         DALLOC(d.Ch, Gp * Gp);
         DALLOC(d.Cl, Gp * Gp);
-        d.tc_ksplit = 1;
-        int ks = c->nbT * (c->nbT + 1) / 2 < 128 ? 8 : 1;
-        while (ks > 1 && (c->Gp / 128) % ks)  // split K (= Gp) into equal multiples of 128
-            ks >>= 1;
-        d.tc_ksplit = ks;
-        if (ks > 1)
-            DALLOC(d.pacc, (size_t)ks * Tp * Tp);
     }
     return 0;
 }
@@ -388,6 +381,7 @@ void free_all(panda_ctx *c)
     drop_graphs(c);
     if (c->stream)
         cudaStreamSynchronize(c->stream);
+    tc_release(c->d);
     for (void *p : c->allocs)
         cudaFree(p);
     c->allocs.clear();
@@ -774,6 +768,21 @@ int panda_set_profiling(panda_ctx *c, int on)
 }
 
 int panda_kernel_count(const panda_ctx *c) { return c ? n_kernels(c) : 0; }
+
+int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms)
+{
+    if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !D || (terms != 1 && terms != 3))
+        return set_err(nullptr, PANDA_EINVAL, "panda_selftest_tc_gemm: bad argument");
+    if (!tc_supported())
+        return set_err(nullptr, PANDA_EUNSUPPORTED, "panda_selftest_tc_gemm: needs an sm_103 device");
+    int status = 0;
+    cudaError_t e = tc_selftest_gemm(M, N, K, A, B, D, terms, &status);
+    if (e != cudaSuccess)
+        return set_err(nullptr, PANDA_ECUDA, std::string("panda_selftest_tc_gemm: ") + cudaGetErrorString(e));
+    if (status & ST_TIMEOUT)
+        return set_err(nullptr, PANDA_ETIMEOUT, "panda_selftest_tc_gemm: a bounded device wait expired");
+    return 0;
+}
 
 int panda_kernel_stats(const panda_ctx *c, int i, char *name, int name_cap, double *total_ms,
                        long long *launches)

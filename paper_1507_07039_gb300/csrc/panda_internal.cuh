@@ -59,8 +59,7 @@ struct Dev {
     // BF16 split copies (tensor-core path only; NULL otherwise)
     __nv_bfloat16 *Wh[2], *Wl[2], *Wth[2], *Wtl[2];
     __nv_bfloat16 *Ph, *Pl, *Ch, *Cl;
-    float *pacc;                 // split-K partial accumulators of W'.W'^T
-    int tc_ksplit;               // split-K factor of the P product
+    void *tc_host;               // host-side tensor maps of the split copies (tensor-core path)
 };
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
@@ -106,12 +105,19 @@ extern const char *const SIMT_KERNEL_NAMES[SIMT_KERNELS];
 cudaError_t launch_iteration_simt(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
 // shared tail of every path: diagonals, norms of P and C, h, stop test
 cudaError_t launch_fin_tail(const Dev &d, cudaStream_t s, KernelEvents &ke);
+// FP64 sums of the per-tile norm partials of W' (shared by both paths)
+cudaError_t launch_reduce_wnorms(const Dev &d, cudaStream_t s);
 
 // ---- tensor-core path (k_tc.cu) --------------------------------------------
-constexpr int TC_KERNELS = 6;
+constexpr int TC_KERNELS = 5;
 extern const char *const TC_KERNEL_NAMES[TC_KERNELS];
 bool tc_supported();
-cudaError_t tc_prepare(Dev &d, cudaStream_t s);  // build the split copies of the state
+cudaError_t tc_prepare(Dev &d, cudaStream_t s);  // split copies of the state, tensor maps
+void tc_release(Dev &d);
 cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
+// D (M x N, row-major) = A (M x K) . B (N x K)^T through the tcgen05 pipeline,
+// host buffers; terms = 1 (hi only) or 3 (split).  *status: device status bits.
+cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms,
+                             int *status);
 
 }  // namespace panda

@@ -65,6 +65,7 @@ def _load() -> ctypes.CDLL:
         "panda_last_error": (ctypes.c_char_p, [vp]),
         "panda_precision_supported": (i, [i]),
         "panda_step_static": (i, [i, i, vp, vp, vp, f, i, i, pd, vp]),
+        "panda_selftest_tc_gemm": (i, [i, i, i, vp, vp, vp, i]),
         "panda_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -236,6 +237,18 @@ def panda_kernel_stats(ctx, i: int):
     ms, n = ctypes.c_double(0.0), ctypes.c_longlong(0)
     _check(lib.panda_kernel_stats(ctx, int(i), name, 64, ctypes.byref(ms), ctypes.byref(n)), ctx)
     return name.value.decode(), ms.value, n.value
+
+
+def panda_selftest_tc_gemm(A, B, terms: int = 3) -> np.ndarray:
+    """D = A . B^T on the tensor-core pipeline (A: M x K, B: N x K, host)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    M, K = A.shape
+    N = B.shape[0]
+    assert B.shape[1] == K
+    D = np.empty((M, N), np.float32)
+    _check(lib.panda_selftest_tc_gemm(M, N, K, _ptr(A), _ptr(B), _ptr(D), int(terms)))
+    return D
 
 
 PANDA_STATIC_MAX_NODES = 512

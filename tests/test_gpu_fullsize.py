@@ -13,7 +13,7 @@ from oracle.oracle import Oracle
 
 pytestmark = pytest.mark.gpu
 
-PRECS = [0]
+PRECS = [0, 1]
 
 
 @pytest.fixture(scope="module")

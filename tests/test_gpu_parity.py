@@ -12,7 +12,7 @@ from paper_1507_07039_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-PRECS = [0]  # PANDA_FP32 (PANDA_BF16X3 joins once its kernels exist)
+PRECS = [0, 1]  # PANDA_FP32, PANDA_BF16X3
 
 
 @pytest.fixture(scope="module")

@@ -1,0 +1,50 @@
+"""The tcgen05 pipeline on its own: D = A . B^T through TMA, the BF16 MMA and
+TMEM, against FP64 products on the host (needs a GB300)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def bf16_split(x: np.ndarray):
+    """hi = bf16(x) (round to nearest even), lo = bf16(x - hi), as float64."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+    hi = t.to(torch.bfloat16).to(torch.float32)
+    lo = (t - hi).to(torch.bfloat16).to(torch.float32)
+    return hi.double().numpy(), lo.double().numpy()
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 260, 200), (129, 385, 1000), (64, 700, 37)])
+def test_hi_only_product(M, N, K):
+    from paper_1507_07039_gb300 import panda
+    rng = np.random.default_rng(M * N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    D = panda.panda_selftest_tc_gemm(A, B, terms=1)
+    Ah, _ = bf16_split(A)
+    Bh, _ = bf16_split(B)
+    ref = Ah @ Bh.T  # products of BF16 values are exact in FP32; only the FP32 sums round
+    err = np.max(np.abs(D - ref)) / max(1.0, np.max(np.abs(ref)))
+    assert err < 2e-6, err
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 512), (130, 300, 1000)])
+def test_three_term_split_product(M, N, K):
+    from paper_1507_07039_gb300 import panda
+    rng = np.random.default_rng(7 * M + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    D = panda.panda_selftest_tc_gemm(A, B, terms=3)
+    Ah, Al = bf16_split(A)
+    Bh, Bl = bf16_split(B)
+    ref3 = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
+    exact = A.astype(np.float64) @ B.astype(np.float64).T
+    scale = max(1.0, np.max(np.abs(exact)))
+    # the tensor core's FP32 accumulation rounds each MMA's K=16 partial into the
+    # accumulator; three MMAs per slice triple the number of such additions
+    assert np.max(np.abs(D - ref3)) / scale < 1e-5
+    # plus the dropped lo*lo term and the split residuals (below 2^-16 relative per product)
+    assert np.max(np.abs(D - exact)) / scale < 3e-5
