@@ -175,7 +175,35 @@ __global__ void k_scan_nonfinite(const float *__restrict__ X, long long n, int *
         atomicOr(flag, 1);
 }
 
+// Lower triangle from the upper one: X[r][c] = X[c][r] for r > c (32 x 32
+// blocks through shared memory, so both sides are read and written along rows).
+__global__ void k_symmetrize(float *X, int n, int ld)
+{
+    __shared__ float tile[32][33];
+    const int bx = blockIdx.x, by = blockIdx.y;  // destination block (row by, column bx)
+    if (by < bx)
+        return;
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    for (int k = ty; k < 32; k += 8) {  // source block (row bx, column by)
+        const int r = bx * 32 + k, c = by * 32 + tx;
+        tile[k][tx] = (r < n && c < n) ? X[(size_t)r * ld + c] : 0.0f;
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int r = by * 32 + k, c = bx * 32 + tx;  // destination (r, c) = source (c, r)
+        if (r < n && c < n && r > c)
+            X[(size_t)r * ld + c] = tile[tx][k];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_symmetrize(float *X, int n, int ld, cudaStream_t s)
+{
+    dim3 grid(ceil_div(n, 32), ceil_div(n, 32)), block(32, 8);
+    k_symmetrize<<<grid, block, 0, s>>>(X, n, ld);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_check_finite_sym(const float *X, int rows, int cols, int ld, bool sym,
                                     int *flags, cudaStream_t s)

@@ -7,10 +7,13 @@
 //                 Tanimoto, damped W update, h and norm partials, and the
 //                 FP32 W' plus its split copies in both orientations.
 //   k_reduce_wnorms  (shared with the FP32 path)
-//   k_tc_phase2   upper-triangle 128 x 128 tiles of W'.W'^T (P, K = genes) and
-//                 W'^T.W' (C, K = TFs) in one launch, P tiles first, with the
-//                 Eq. 5 epilogue: Tanimoto, damped update, mirrored FP32 and
-//                 split stores, row partial sums for Eq. 6.
+//   k_tc_phase2   persistent: upper-triangle 128 x 128 tiles of W'.W'^T (P,
+//                 K = genes) and W'^T.W' (C, K = TFs) from a balanced host-built
+//                 schedule, double-buffered TMEM accumulators, and the Eq. 5
+//                 epilogue: Tanimoto, damped update, the FP32 upper triangle,
+//                 split copies of both triangles, row partial sums for Eq. 6.
+//                 (Only the upper triangle of FP32 P and C is ever read here;
+//                 panda_get and panda_save mirror it first.)
 //   k_fin, k_tail (shared): Eq. 6 diagonals, norms, h, stop test.
 //
 // C and P are symmetric, so "C_off rows" and "P_off rows" are the K-major
@@ -18,7 +21,10 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
+#include <queue>
+#include <vector>
 
 #include "panda_internal.cuh"
 #include "tc_common.cuh"
@@ -328,158 +334,296 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_phase1(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Phase 2 (grid: upper-triangle tiles of P, then of C)
+// Phase 2: persistent CTAs over a host-built schedule of upper-triangle
+// 128 x 128 tiles of W'.W'^T (P, K = genes) and W'^T.W' (C, K = TFs).  Two
+// TMEM accumulators alternate, so the epilogue of one tile overlaps the MMAs
+// of the next.  Warps: 0 TMA, 1 MMA, 2-9 epilogue (two per TMEM lane quarter,
+// each taking 64 of the 128 columns).
 // ---------------------------------------------------------------------------
+constexpr int EPI2 = 8;
+constexpr int THREADS2 = 64 + 32 * EPI2;
+constexpr uint32_t STAGE2 = 4 * A_BYTES;  // A hi, A lo, B hi, B lo (B is 128 rows too)
+
+struct Sync2 {
+    uint64_t full[ST2], empty[ST2];
+    uint64_t tfull[2], tempty[2];  // accumulator ready / accumulator drained
+    uint32_t tmem;
+    int abort, issued, consumed;
+};
+
+constexpr size_t P2_COLRED = 4 * 3 * 128;  // [quarter][sum][column] floats
+constexpr size_t P2_ROWRED = 2 * 3 * 128;  // [half][sum][row] floats
+constexpr size_t P2_XPOSE = 32 * 34;       // per epilogue warp, uint16
+
 constexpr size_t phase2_smem()
 {
-    return 1024 + (size_t)ST2 * (4 * A_BYTES) + sizeof(Sync<ST2>) + 16 + 3 * 4 * 128 * sizeof(float) +
-           3 * 128 * sizeof(float);
+    return 1024 + (size_t)ST2 * STAGE2 + ((sizeof(Sync2) + 15) & ~size_t(15)) +
+           (P2_COLRED + P2_ROWRED) * sizeof(float) + EPI2 * P2_XPOSE * sizeof(uint16_t);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+{
+    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Write 32 BF16 values to dst[0..31]: vector stores when all are valid, else
+// only the entries whose bit is set in mask.
+__device__ __forceinline__ void st32_bf16_masked(__nv_bfloat16 *dst, const __nv_bfloat16 (&v)[32], uint32_t mask)
+{
+    if (mask == 0xffffffffu) {
+        st32_bf16(dst, v);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (mask >> q & 1u)
+                dst[q] = v[q];
+    }
+}
+
+// The warp's 32 x 32 block of BF16 values (row = lane, column = q) is written
+// transposed: lane l stores column l as a row of 32 values at dst_row(l).
+__device__ __forceinline__ void store_transposed(uint16_t *xp, const __nv_bfloat16 (&v)[32], __nv_bfloat16 *dst,
+                                                 uint32_t mask)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        xp[lane * 34 + q] = __bfloat16_as_ushort(v[q]);
+    __syncwarp();
+    __nv_bfloat16 t[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+        t[q] = __ushort_as_bfloat16(xp[q * 34 + lane]);
+    __syncwarp();
+    if (dst)
+        st32_bf16_masked(dst, t, mask);
 }
 
 template <bool SIM_SIGMA>
-__global__ void __launch_bounds__(THREADS, 1) k_tc_phase2(const __grid_constant__ TcMaps maps, Dev d, int cur)
+__global__ void __launch_bounds__(THREADS2, 1)
+    k_tc_phase2(const __grid_constant__ TcMaps maps, Dev d, int cur, const int *__restrict__ sched_off,
+                const int *__restrict__ sched)
 {
     Ctl *ctl = d.ctl;
     if (!ctl->active)
         return;
-    constexpr int BN = 128, STAGES = ST2;
-    constexpr uint32_t B_BYTES = BN * BK * 2, STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    constexpr int BN = 128;
+    constexpr uint32_t B_BYTES = BN * BK * 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
-    Sync<STAGES> &sy = *reinterpret_cast<Sync<STAGES> *>(stages + STAGES * STAGE);
-    float *colred = reinterpret_cast<float *>(stages + STAGES * STAGE + ((sizeof(Sync<STAGES>) + 15) & ~15));
-    float *rowred = colred + 3 * 4 * BN;  // [3][128]
+    Sync2 &sy = *reinterpret_cast<Sync2 *>(stages + ST2 * STAGE2);
+    float *colred = reinterpret_cast<float *>(stages + ST2 * STAGE2 + ((sizeof(Sync2) + 15) & ~size_t(15)));
+    float *rowred = colred + P2_COLRED;
+    uint16_t *xpose = reinterpret_cast<uint16_t *>(rowred + P2_ROWRED);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nP = d.nbT * (d.nbT + 1) / 2;
-    const bool isP = (int)blockIdx.x < nP;
-    int bm, bn;
-    tri_decode(isP ? (int)blockIdx.x : (int)blockIdx.x - nP, isP ? d.nbT : d.nbG, bm, bn);
-    const int m0 = bm * BM, n0 = bn * BN;
-    const int nk = (isP ? d.Gp : d.Tp) / BK;
-    const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Wth2[cur];
-    const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl2[cur];
+    const int first = sched_off[blockIdx.x], last = sched_off[blockIdx.x + 1];
 
-    if (threadIdx.x == 0)
-        init_sync(sy);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < ST2; ++q) {
+            mbar_init(&sy.full[q], 1);
+            mbar_init(&sy.empty[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&sy.tfull[q], 1);
+            mbar_init(&sy.tempty[q], EPI2);
+        }
+        sy.abort = 0;
+        sy.issued = 0;
+        sy.consumed = 0;
+        fence_mbar_init();
+    }
     if (warp == 1)
-        tmem_alloc(&sy.tmem, BN);
+        tmem_alloc(&sy.tmem, 2 * BN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
 
     if (warp == 0) {
-        if (lane == 0)
-            run_producer<STAGES>(sy, stages, STAGE, nk, ctl, [&](int kb, uint8_t *st, uint64_t *bar) {
-                const int k = kb * BK;
-                tma_load_2d(st, mh, bar, k, m0);
-                tma_load_2d(st + A_BYTES, ml, bar, k, m0);
-                tma_load_2d(st + 2 * A_BYTES, mh, bar, k, n0);
-                tma_load_2d(st + 2 * A_BYTES + B_BYTES, ml, bar, k, n0);
-            });
+        if (lane == 0) {  // ---- TMA producer ----
+            int g = 0;
+            bool ok = true;
+            for (int n = first; n < last && ok; ++n) {
+                const int tile = sched[n];
+                const bool isP = tile < 0;
+                const int m0 = ((tile >> 16) & 0x7fff) * BM, n0 = (tile & 0xffff) * BN;
+                const int nk = (isP ? d.Gp : d.Tp) / BK;
+                const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Wth2[cur];
+                const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl2[cur];
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int st = g % ST2;
+                    if (!wait_bounded(&sy.empty[st], ((uint32_t)(g / ST2) & 1u) ^ 1u, &sy.abort, ctl)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *b = stages + (size_t)st * STAGE2;
+                    mbar_arrive_expect_tx(&sy.full[st], STAGE2);
+                    tma_load_2d(b, mh, &sy.full[st], kb * BK, m0);
+                    tma_load_2d(b + A_BYTES, ml, &sy.full[st], kb * BK, m0);
+                    tma_load_2d(b + 2 * A_BYTES, mh, &sy.full[st], kb * BK, n0);
+                    tma_load_2d(b + 2 * A_BYTES + B_BYTES, ml, &sy.full[st], kb * BK, n0);
+                }
+            }
+            sy.issued = g;
+        }
     } else if (warp == 1) {
-        if (lane == 0)
-            run_mma<STAGES, BN>(sy, stages, STAGE, nk, ctl, [](int) { return 0u; }, [](int kb) { return kb == 0; });
-    } else {
-        const int wq = warp & 3, ew = warp - 2;
+        if (lane == 0) {  // ---- MMA issuer ----
+            constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+            int g = 0;
+            bool ok = true;
+            for (int n = first, idx = 0; n < last && ok; ++n, ++idx) {
+                const int tile = sched[n];
+                const int nk = (tile < 0 ? d.Gp : d.Tp) / BK;
+                const int buf = idx & 1;
+                if (!wait_bounded(&sy.tempty[buf], ((uint32_t)(idx >> 1) & 1u) ^ 1u, &sy.abort, ctl))
+                    break;
+                tc_fence_after();
+                const uint32_t dacc = sy.tmem + buf * BN;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int st = g % ST2;
+                    if (!wait_bounded(&sy.full[st], (uint32_t)(g / ST2) & 1u, &sy.abort, ctl)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(stages + (size_t)st * STAGE2);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        const uint64_t ah = sdesc_k_sw128(base + off);
+                        const uint64_t al = sdesc_k_sw128(base + A_BYTES + off);
+                        const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
+                        const uint64_t bl = sdesc_k_sw128(base + 2 * A_BYTES + B_BYTES + off);
+                        mma_bf16(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                        mma_bf16(dacc, ah, bl, idesc, 1u);
+                        mma_bf16(dacc, al, bh, idesc, 1u);
+                    }
+                    mma_commit(&sy.empty[st]);
+                }
+                mma_commit(&sy.tfull[buf]);
+            }
+            sy.consumed = g;
+        }
+    } else {  // ---- epilogue: warps 2..9 ----
+        const int e = warp - 2, wq = warp & 3, half = e >> 2;
         const int r = wq * 32 + lane;
-        const int n = isP ? d.T : d.G, ld = isP ? d.Tp : d.Gp;
-        const float *nrm = isP ? d.rsqW : d.csqW;
-        float *X = isP ? d.Poff : d.Coff;
-        __nv_bfloat16 *Xh = isP ? d.Ph : d.Ch, *Xl = isP ? d.Pl : d.Cl;
-        const int k = m0 + r;
-        const bool ok = wait_bounded(&sy.accum, 0, &sy.abort, ctl);
-        tc_fence_after();
-        const bool live = ok && !*(volatile int *)&sy.abort;
-        float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
-        if (live) {
-            const float a = ctl->alpha, keep = 1.0f - a;
-            const float nk_ = k < n ? nrm[k] : 0.0f;
-            const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
+        uint16_t *xp = xpose + (size_t)e * P2_XPOSE;
+        const int tt = threadIdx.x - 64;  // 0..255
+        const float a = ctl->alpha, keep = 1.0f - a;
+        for (int n = first, idx = 0; n < last; ++n, ++idx) {
+            const int tile = sched[n];
+            const bool isP = tile < 0;
+            const int bm = (tile >> 16) & 0x7fff, bn = tile & 0xffff;
+            const int m0 = bm * BM, n0 = bn * BN;
+            const int nn = isP ? d.T : d.G, ld = isP ? d.Tp : d.Gp;
+            const float *nrm = isP ? d.rsqW : d.csqW;
+            float *X = isP ? d.Poff : d.Coff;
+            __nv_bfloat16 *Xh = isP ? d.Ph : d.Ch, *Xl = isP ? d.Pl : d.Cl;
+            const int buf = idx & 1;
+            // on a timed-out wait every epilogue warp still runs the named barriers below
+            const bool live = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, ctl) &&
+                              !*(volatile int *)&sy.abort;
+            tc_fence_after();
+            const int k = m0 + r, k0 = m0 + wq * 32;
+            const float nk_ = k < nn ? nrm[k] : 0.0f;
+            float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                const int j0 = n0 + c * 32;
+            for (int c = 0; c < 2 && live; ++c) {
+                const int cc = half * 2 + c, j0 = n0 + cc * 32;
                 float acc[32], old[32];
-                tmem_ld32(trow + c * 32, acc);
+                tmem_ld32(sy.tmem + buf * BN + ((uint32_t)(wq * 32) << 16) + cc * 32, acc);
+                if (c == 1) {  // this warp is done with the accumulator
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive(&sy.tempty[buf]);
+                }
                 ld32(X + (size_t)k * ld + j0, old);
-                float c1[32], c2[32], cv[32];
-                bool all = true;
+                uint32_t vmask = 0;
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     const int j = j0 + q;
-                    const bool valid = k < j && j < n;
-                    all = all && valid;
-                    c1[q] = c2[q] = cv[q] = 0.0f;
-                    if (valid) {
-                        const float s = tanimoto_f(acc[q], nk_, nrm[j]);
-                        const float v = keep * old[q] + a * s;
-                        const float x = SIM_SIGMA ? s : v;
+                    float x = 0.0f;
+                    if (k < j && j < nn) {
+                        const float sv = tanimoto_f(acc[q], nk_, nrm[j]);
+                        const float v = keep * old[q] + a * sv;
+                        x = SIM_SIGMA ? sv : v;
                         r1 += x; r2 += x * x; rv += v * v;
-                        c1[q] = x; c2[q] = x * x; cv[q] = v * v;
-                        old[q] = v;  // now the value to store
+                        old[q] = v;
+                        vmask |= 1u << q;
                     }
-                    acc[q] = valid ? 1.0f : 0.0f;  // validity mask from here on
+                    acc[q] = x;
                 }
+                // column sums over this warp's 32 rows
+                float tmp[32];
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    tmp[q] = acc[q];
+                colred[(wq * 3 + 0) * 128 + cc * 32 + lane] = lane_transpose_sum(tmp);
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    tmp[q] = acc[q] * acc[q];
+                colred[(wq * 3 + 1) * 128 + cc * 32 + lane] = lane_transpose_sum(tmp);
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    tmp[q] = (vmask >> q & 1u) ? old[q] * old[q] : 0.0f;
+                colred[(wq * 3 + 2) * 128 + cc * 32 + lane] = lane_transpose_sum(tmp);
+                // row stores: FP32 upper triangle only, split copies in both orientations
                 __nv_bfloat16 hv[32], lv[32];
 #pragma unroll
                 for (int q = 0; q < 32; ++q)
                     split_bf16(old[q], hv[q], lv[q]);
                 const size_t o = (size_t)k * ld + j0;
-                if (all) {
+                if (vmask == 0xffffffffu) {
                     st32(X + o, old);
-                    st32_bf16(Xh + o, hv);
-                    st32_bf16(Xl + o, lv);
                 } else {
 #pragma unroll
                     for (int q = 0; q < 32; ++q)
-                        if (acc[q] != 0.0f) {
+                        if (vmask >> q & 1u)
                             X[o + q] = old[q];
-                            Xh[o + q] = hv[q];
-                            Xl[o + q] = lv[q];
-                        }
                 }
+                st32_bf16_masked(Xh + o, hv, vmask);
+                st32_bf16_masked(Xl + o, lv, vmask);
+                // mirrored entries (j, k): lane l writes row j0 + l, columns k0 .. k0 + 31
+                const int jm = j0 + lane;
+                const uint32_t mmask = jm >= nn ? 0u : (k0 + 31 < jm ? 0xffffffffu : (k0 >= jm ? 0u : ((1u << (jm - k0)) - 1u)));
+                const size_t mo = (size_t)jm * ld + k0;
+                store_transposed(xp, hv, mmask ? Xh + mo : nullptr, mmask);
+                store_transposed(xp, lv, mmask ? Xl + mo : nullptr, mmask);
+            }
+            rowred[(half * 3 + 0) * 128 + r] = r1;
+            rowred[(half * 3 + 1) * 128 + r] = r2;
+            rowred[(half * 3 + 2) * 128 + r] = rv;
+            epi_bar2();
+            if (tt < 128 && live) {
 #pragma unroll
-                for (int q = 0; q < 32; ++q)  // mirrored entries: lanes write consecutive rows
-                    if (acc[q] != 0.0f) {
-                        const size_t mo = (size_t)(j0 + q) * ld + k;
-                        X[mo] = old[q];
-                        Xh[mo] = hv[q];
-                        Xl[mo] = lv[q];
+                for (int w = 0; w < 3; ++w) {
+                    float *S = w == 0 ? (isP ? d.ps_sum : d.cs_sum) : w == 1 ? (isP ? d.ps_sq : d.cs_sq)
+                                                                            : (isP ? d.ps_vsq : d.cs_vsq);
+                    const float cs = ((colred[(0 * 3 + w) * 128 + tt] + colred[(1 * 3 + w) * 128 + tt]) +
+                                      colred[(2 * 3 + w) * 128 + tt]) + colred[(3 * 3 + w) * 128 + tt];
+                    const float rs = rowred[(0 * 3 + w) * 128 + tt] + rowred[(1 * 3 + w) * 128 + tt];
+                    if (bm == bn) {
+                        S[(size_t)bm * ld + m0 + tt] = rs + cs;
+                    } else {
+                        S[(size_t)bn * ld + m0 + tt] = rs;  // rows of this tile, slot of its column block
+                        S[(size_t)bm * ld + n0 + tt] = cs;  // mirrored rows, slot of its row block
                     }
-                colred[(0 * 4 + ew) * BN + c * 32 + lane] = lane_transpose_sum(c1);
-                colred[(1 * 4 + ew) * BN + c * 32 + lane] = lane_transpose_sum(c2);
-                colred[(2 * 4 + ew) * BN + c * 32 + lane] = lane_transpose_sum(cv);
-            }
-        }
-        rowred[0 * BN + r] = r1;
-        rowred[1 * BN + r] = r2;
-        rowred[2 * BN + r] = rv;
-        epi_bar();
-        const int t = threadIdx.x - 64;
-        if (live) {
-            float *S[3] = {isP ? d.ps_sum : d.cs_sum, isP ? d.ps_sq : d.cs_sq, isP ? d.ps_vsq : d.cs_vsq};
-#pragma unroll
-            for (int w = 0; w < 3; ++w) {
-                const float cs = ((colred[(w * 4 + 0) * BN + t] + colred[(w * 4 + 1) * BN + t]) +
-                                  colred[(w * 4 + 2) * BN + t]) + colred[(w * 4 + 3) * BN + t];
-                const float rs = rowred[w * BN + t];
-                if (bm == bn) {
-                    S[w][(size_t)bm * ld + m0 + t] = rs + cs;
-                } else {
-                    S[w][(size_t)bn * ld + m0 + t] = rs;  // rows of this tile, slot of its column block
-                    S[w][(size_t)bm * ld + n0 + t] = cs;  // mirrored rows, slot of its row block
                 }
             }
+            epi_bar2();
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0)
-        drain(sy, ctl);
+    if (threadIdx.x == 0) {  // drain: loads issued but not consumed, and the last MMAs
+        for (int g = sy.consumed; g < sy.issued; ++g)
+            wait_bounded(&sy.full[g % ST2], (uint32_t)(g / ST2) & 1u, &sy.abort, ctl, true);
+    }
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(sy.tmem, BN);
+        tmem_dealloc(sy.tmem, 2 * BN);
     }
 }
 
@@ -515,6 +659,48 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int rows, int cols, int b
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+struct TcHost {
+    TcMaps maps;
+    int *sched_off = nullptr;  // [grid2 + 1] offsets into sched
+    int *sched = nullptr;      // packed tiles: bit 31 = P, bits 16-30 = row block, bits 0-15 = column block
+    int grid2 = 0;
+};
+
+// Longest-processing-time assignment of the upper-triangle tiles of P and C to
+// `ctas` persistent CTAs; cost of a tile = its k-blocks + a fixed epilogue share.
+void build_schedule(const Dev &d, int ctas, std::vector<int> &off, std::vector<int> &tiles)
+{
+    struct T_ { int cost, code; };
+    std::vector<T_> all;
+    const int kP = d.Gp / BK, kC = d.Tp / BK, epi = 8;
+    for (int bm = 0; bm < d.nbT; ++bm)
+        for (int bn = bm; bn < d.nbT; ++bn)
+            all.push_back({kP + epi, (int)(0x80000000u | ((uint32_t)bm << 16) | (uint32_t)bn)});
+    for (int bm = 0; bm < d.nbG; ++bm)
+        for (int bn = bm; bn < d.nbG; ++bn)
+            all.push_back({kC + epi, (bm << 16) | bn});
+    std::stable_sort(all.begin(), all.end(), [](const T_ &a, const T_ &b) { return a.cost > b.cost; });
+    if (ctas > (int)all.size())
+        ctas = (int)all.size();
+    std::vector<std::vector<int>> lists(ctas);
+    using L = std::pair<long long, int>;
+    std::priority_queue<L, std::vector<L>, std::greater<L>> heap;
+    for (int c = 0; c < ctas; ++c)
+        heap.push({0, c});
+    for (const auto &t : all) {
+        L top = heap.top();
+        heap.pop();
+        lists[top.second].push_back(t.code);
+        heap.push({top.first + t.cost, top.second});
+    }
+    off.assign(1, 0);
+    tiles.clear();
+    for (const auto &l : lists) {
+        tiles.insert(tiles.end(), l.begin(), l.end());
+        off.push_back((int)tiles.size());
+    }
 }
 
 cudaError_t set_smem_limits()
@@ -567,37 +753,51 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s)
     if ((e = cudaGetLastError()))
         return e;
     if (!d.tc_host) {
-        TcMaps *m = new TcMaps;
+        TcHost *h = new TcHost;
+        TcMaps *m = &h->maps;
         std::memset(m, 0, sizeof *m);
+        d.tc_host = h;
         if ((e = make_map(&m->Ph, d.Ph, d.Tp, d.Tp, 128)) || (e = make_map(&m->Pl, d.Pl, d.Tp, d.Tp, 128)) ||
-            (e = make_map(&m->Ch1, d.Ch, d.Gp, d.Gp, BN1)) || (e = make_map(&m->Cl1, d.Cl, d.Gp, d.Gp, BN1))) {
-            delete m;
+            (e = make_map(&m->Ch1, d.Ch, d.Gp, d.Gp, BN1)) || (e = make_map(&m->Cl1, d.Cl, d.Gp, d.Gp, BN1)))
             return e;
-        }
         for (int b = 0; b < 2; ++b)
             if ((e = make_map(&m->Wh[b], d.Wh[b], d.Tp, d.Gp, 128)) ||
                 (e = make_map(&m->Wl[b], d.Wl[b], d.Tp, d.Gp, 128)) ||
                 (e = make_map(&m->Wth1[b], d.Wth[b], d.Gp, d.Tp, BN1)) ||
                 (e = make_map(&m->Wtl1[b], d.Wtl[b], d.Gp, d.Tp, BN1)) ||
                 (e = make_map(&m->Wth2[b], d.Wth[b], d.Gp, d.Tp, 128)) ||
-                (e = make_map(&m->Wtl2[b], d.Wtl[b], d.Gp, d.Tp, 128))) {
-                delete m;
+                (e = make_map(&m->Wtl2[b], d.Wtl[b], d.Gp, d.Tp, 128)))
                 return e;
-            }
-        d.tc_host = m;
+        int dev = 0, nsm = 0;
+        if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
+            return e;
+        std::vector<int> off, tiles;
+        build_schedule(d, nsm, off, tiles);
+        h->grid2 = (int)off.size() - 1;
+        if ((e = cudaMalloc(&h->sched_off, off.size() * sizeof(int))) ||
+            (e = cudaMalloc(&h->sched, tiles.size() * sizeof(int))) ||
+            (e = cudaMemcpy(h->sched_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(h->sched, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice)))
+            return e;
     }
     return cudaSuccess;
 }
 
 void tc_release(Dev &d)
 {
-    delete static_cast<TcMaps *>(d.tc_host);
+    TcHost *h = static_cast<TcHost *>(d.tc_host);
+    if (h) {
+        cudaFree(h->sched_off);
+        cudaFree(h->sched);
+        delete h;
+    }
     d.tc_host = nullptr;
 }
 
 cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke)
 {
-    const TcMaps &m = *static_cast<const TcMaps *>(d.tc_host);
+    const TcHost &h = *static_cast<const TcHost *>(d.tc_host);
+    const TcMaps &m = h.maps;
     ke.mark(s);
     dim3 g1(d.nbT, ceil_div(d.Gp, BN1));
     k_tc_phase1<<<g1, THREADS, phase1_smem(), s>>>(m, d, cur);
@@ -606,11 +806,10 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
     if (e)
         return e;
     ke.mark(s);
-    const int tiles = d.nbT * (d.nbT + 1) / 2 + d.nbG * (d.nbG + 1) / 2;
     if (d.diag == 2)
-        k_tc_phase2<true><<<tiles, THREADS, phase2_smem(), s>>>(m, d, cur ^ 1);
+        k_tc_phase2<true><<<h.grid2, THREADS2, phase2_smem(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
     else
-        k_tc_phase2<false><<<tiles, THREADS, phase2_smem(), s>>>(m, d, cur ^ 1);
+        k_tc_phase2<false><<<h.grid2, THREADS2, phase2_smem(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
     ke.mark(s);
     return launch_fin_tail(d, s, ke);
 }

@@ -557,9 +557,21 @@ int panda_run(panda_ctx *c, float alpha, double tol, int max_iter, int *iters_ou
     return c->h_ctl->converged ? PANDA_OK : PANDA_NOT_CONVERGED;
 }
 
+// The tensor-core path keeps only the upper triangle of FP32 P and C current.
+static int full_matrices(panda_ctx *c)
+{
+    if (c->prec == PANDA_BF16X3) {
+        CU(launch_symmetrize(c->d.Poff, c->T, c->Tp, c->stream));
+        CU(launch_symmetrize(c->d.Coff, c->G, c->Gp, c->stream));
+    }
+    return 0;
+}
+
 static int get_impl(panda_ctx *c, float *W, float *P, float *C)
 {
     Dev &d = c->d;
+    if ((P || C) && full_matrices(c))
+        return PANDA_ECUDA;
     if (W) {
         int rc = download(c, W, d.W[c->cur], c->Gp, c->T, c->G);
         if (rc)
@@ -679,6 +691,8 @@ int panda_save(panda_ctx *c, void *buf, long long bytes)
     CkptHeader h{};
     std::memcpy(h.magic, "PANDAGB", 8);
     h.version = 1; h.T = c->T; h.G = c->G; h.prec = c->prec; h.diag = c->diag; h.iters = c->h_ctl->iters;
+    if (full_matrices(c))
+        return PANDA_ECUDA;
     char *p = static_cast<char *>(buf);
     std::memcpy(p, &h, sizeof h);
     p += sizeof h;

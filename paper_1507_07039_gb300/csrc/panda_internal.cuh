@@ -86,6 +86,8 @@ cudaError_t launch_col_norms(const float *X, int rows, int cols, int ld, float *
                              cudaStream_t s);
 cudaError_t launch_diag_to_float(const double *d, float *df, int n, cudaStream_t s);
 cudaError_t launch_scan_nonfinite(const float *X, long long n, int *flag, cudaStream_t s);
+// X[r][c] = X[c][r] for r > c: the full matrix from its upper triangle
+cudaError_t launch_symmetrize(float *X, int n, int ld, cudaStream_t s);
 
 // Optional per-kernel timing: when ev is not NULL, ev[0] is recorded before the
 // first kernel of the iteration and ev[k + 1] after kernel k.

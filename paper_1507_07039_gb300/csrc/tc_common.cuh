@@ -270,7 +270,14 @@ __device__ __forceinline__ float lane_transpose_sum(float (&v)[32])
     return v[0];
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// named barriers among the epilogue warps only (128 or 256 threads)
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar2() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
 }  // namespace tc
 }  // namespace panda
