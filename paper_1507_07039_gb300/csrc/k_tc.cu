@@ -61,6 +61,16 @@ __device__ __forceinline__ void split_bf16(float x, __nv_bfloat16 &hi, __nv_bflo
     lo = __float2bfloat16_rn(x - __bfloat162float(hi));  // x - hi is exact in FP32
 }
 
+// Eq. 1 from the numerator and the two squared norms with the hardware
+// reciprocal square root (rsqrtf, within 2 ulp): the tensor-core path's
+// epilogues, whose products carry BF16X3 error far above that; 0 when the
+// denominator is 0 (both vectors zero).
+__device__ __forceinline__ float tanimoto_fast(float num, float nx, float ny)
+{
+    const float den = (nx + ny) - fabsf(num);
+    return den > 0.0f ? num * rsqrtf(den) : 0.0f;
+}
+
 // hi / lo of a whole array (padding stays zero because x is zero there)
 __global__ void k_split(const float *__restrict__ X, size_t n, __nv_bfloat16 *__restrict__ H,
                         __nv_bfloat16 *__restrict__ L)
@@ -279,8 +289,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_phase1(const __grid_constant_
                     if (ri && j < d.G) {
                         const float rnum = rr[q] + pdi * w[q];       // P_i. . W_.j
                         const float anum = aa[q] + w[q] * d.cdf[j];  // W_i. . C_.j
-                        const float R = tanimoto_f(rnum, rsp, d.csqW[j]);
-                        const float A = tanimoto_f(anum, rsw, d.csqC[j]);
+                        const float R = tanimoto_fast(rnum, rsp, d.csqW[j]);
+                        const float A = tanimoto_fast(anum, rsw, d.csqC[j]);
                         wn[q] = keep * w[q] + half * (A + R);
                         hsum += fabsf(wn[q] - w[q]);
                         rowsq += wn[q] * wn[q];
@@ -366,37 +376,41 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
     return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// Write 32 BF16 values to dst[0..31]: vector stores when all are valid, else
-// only the entries whose bit is set in mask.
-__device__ __forceinline__ void st32_bf16_masked(__nv_bfloat16 *dst, const __nv_bfloat16 (&v)[32], uint32_t mask)
+// 32 BF16 values held as 16 packed pairs (element 2p in the low half of p[p]).
+__device__ __forceinline__ void st32_packed(__nv_bfloat16 *dst, const uint32_t (&p)[16], uint32_t mask)
 {
     if (mask == 0xffffffffu) {
-        st32_bf16(dst, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            reinterpret_cast<uint4 *>(dst)[q] = make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
     } else {
+        uint16_t *d16 = reinterpret_cast<uint16_t *>(dst);
 #pragma unroll
         for (int q = 0; q < 32; ++q)
             if (mask >> q & 1u)
-                dst[q] = v[q];
+                d16[q] = (uint16_t)(p[q >> 1] >> (16 * (q & 1)));
     }
 }
 
-// The warp's 32 x 32 block of BF16 values (row = lane, column = q) is written
-// transposed: lane l stores column l as a row of 32 values at dst_row(l).
-__device__ __forceinline__ void store_transposed(uint16_t *xp, const __nv_bfloat16 (&v)[32], __nv_bfloat16 *dst,
+// The warp's 32 x 32 block of BF16 values (row = lane, column = q, packed)
+// is written transposed: lane l stores column l as the 32 values of row
+// dst (shared memory rows of 34 halves keep both passes free of conflicts).
+__device__ __forceinline__ void store_transposed(uint16_t *xp, const uint32_t (&p)[16], __nv_bfloat16 *dst,
                                                  uint32_t mask)
 {
     const int lane = threadIdx.x & 31;
+    uint32_t *xp32 = reinterpret_cast<uint32_t *>(xp);
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
-        xp[lane * 34 + q] = __bfloat16_as_ushort(v[q]);
+    for (int q = 0; q < 16; ++q)
+        xp32[lane * 17 + q] = p[q];
     __syncwarp();
-    __nv_bfloat16 t[32];
+    uint32_t t[16];
 #pragma unroll
-    for (int q = 0; q < 32; ++q)
-        t[q] = __ushort_as_bfloat16(xp[q * 34 + lane]);
+    for (int q = 0; q < 16; ++q)
+        t[q] = (uint32_t)xp[(2 * q) * 34 + lane] | ((uint32_t)xp[(2 * q + 1) * 34 + lane] << 16);
     __syncwarp();
     if (dst)
-        st32_bf16_masked(dst, t, mask);
+        st32_packed(dst, t, mask);
 }
 
 template <bool SIM_SIGMA>
@@ -530,50 +544,49 @@ __global__ void __launch_bounds__(THREADS2, 1)
 #pragma unroll 1
             for (int c = 0; c < 2 && live; ++c) {
                 const int cc = half * 2 + c, j0 = n0 + cc * 32;
+                const size_t o = (size_t)k * ld + j0;
                 float acc[32], old[32];
-                tmem_ld32(sy.tmem + buf * BN + ((uint32_t)(wq * 32) << 16) + cc * 32, acc);
+                ld32(X + o, old);                                           // global loads first,
+                const float nj = j0 + lane < nn ? nrm[j0 + lane] : 0.0f;    // column norms, one per lane,
+                tmem_ld32(sy.tmem + buf * BN + ((uint32_t)(wq * 32) << 16) + cc * 32, acc);  // then TMEM
                 if (c == 1) {  // this warp is done with the accumulator
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0)
                         mbar_arrive(&sy.tempty[buf]);
                 }
-                ld32(X + (size_t)k * ld + j0, old);
-                uint32_t vmask = 0;
+                // interior chunks of off-diagonal tiles are entirely valid
+                const bool all = k < j0 && j0 + 31 < nn;
+                uint32_t vmask = 0xffffffffu;
+                if (!all) {
+                    vmask = 0;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        vmask |= (k < j0 + q && j0 + q < nn) ? (1u << q) : 0u;
+                }
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
-                    const int j = j0 + q;
-                    float x = 0.0f;
-                    if (k < j && j < nn) {
-                        const float sv = tanimoto_f(acc[q], nk_, nrm[j]);
-                        const float v = keep * old[q] + a * sv;
-                        x = SIM_SIGMA ? sv : v;
-                        r1 += x; r2 += x * x; rv += v * v;
-                        old[q] = v;
-                        vmask |= 1u << q;
-                    }
+                    const float s = tanimoto_fast(acc[q], nk_, __shfl_sync(0xffffffffu, nj, q));
+                    const bool valid = (vmask >> q) & 1u;
+                    const float v = valid ? fmaf(a, s, keep * old[q]) : old[q];
+                    const float x = valid ? (SIM_SIGMA ? s : v) : 0.0f;
+                    r1 += x;
+                    r2 += x * x;
+                    if (SIM_SIGMA)
+                        rv += valid ? v * v : 0.0f;
+                    old[q] = v;
                     acc[q] = x;
                 }
-                // column sums over this warp's 32 rows
-                float tmp[32];
+                // stores: FP32 upper triangle, split copies in both orientations
+                uint32_t hv[16], lv[16];
 #pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    tmp[q] = acc[q];
-                colred[(wq * 3 + 0) * 128 + cc * 32 + lane] = lane_transpose_sum(tmp);
-#pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    tmp[q] = acc[q] * acc[q];
-                colred[(wq * 3 + 1) * 128 + cc * 32 + lane] = lane_transpose_sum(tmp);
-#pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    tmp[q] = (vmask >> q & 1u) ? old[q] * old[q] : 0.0f;
-                colred[(wq * 3 + 2) * 128 + cc * 32 + lane] = lane_transpose_sum(tmp);
-                // row stores: FP32 upper triangle only, split copies in both orientations
-                __nv_bfloat16 hv[32], lv[32];
-#pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    split_bf16(old[q], hv[q], lv[q]);
-                const size_t o = (size_t)k * ld + j0;
+                for (int q = 0; q < 16; ++q) {
+                    __nv_bfloat16 h0, l0, h1, l1;
+                    split_bf16(old[2 * q], h0, l0);
+                    split_bf16(old[2 * q + 1], h1, l1);
+                    hv[q] = pack2(h0, h1);
+                    lv[q] = pack2(l0, l1);
+                }
                 if (vmask == 0xffffffffu) {
                     st32(X + o, old);
                 } else {
@@ -582,15 +595,29 @@ __global__ void __launch_bounds__(THREADS2, 1)
                         if (vmask >> q & 1u)
                             X[o + q] = old[q];
                 }
-                st32_bf16_masked(Xh + o, hv, vmask);
-                st32_bf16_masked(Xl + o, lv, vmask);
+                st32_packed(Xh + o, hv, vmask);
+                st32_packed(Xl + o, lv, vmask);
                 // mirrored entries (j, k): lane l writes row j0 + l, columns k0 .. k0 + 31
                 const int jm = j0 + lane;
                 const uint32_t mmask = jm >= nn ? 0u : (k0 + 31 < jm ? 0xffffffffu : (k0 >= jm ? 0u : ((1u << (jm - k0)) - 1u)));
                 const size_t mo = (size_t)jm * ld + k0;
                 store_transposed(xp, hv, mmask ? Xh + mo : nullptr, mmask);
                 store_transposed(xp, lv, mmask ? Xl + mo : nullptr, mmask);
+                // column sums over this warp's 32 rows (x in acc; under D2 also v^2)
+                if (SIM_SIGMA) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        old[q] = (vmask >> q & 1u) ? old[q] * old[q] : 0.0f;
+                    colred[(wq * 3 + 2) * 128 + cc * 32 + lane] = lane_transpose_sum(old);
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    old[q] = acc[q] * acc[q];
+                colred[(wq * 3 + 1) * 128 + cc * 32 + lane] = lane_transpose_sum(old);
+                colred[(wq * 3 + 0) * 128 + cc * 32 + lane] = lane_transpose_sum(acc);
             }
+            if (!SIM_SIGMA)
+                rv = r2;  // x = v under rules D1 and D0
             rowred[(half * 3 + 0) * 128 + r] = r1;
             rowred[(half * 3 + 1) * 128 + r] = r2;
             rowred[(half * 3 + 2) * 128 + r] = rv;
@@ -600,8 +627,9 @@ __global__ void __launch_bounds__(THREADS2, 1)
                 for (int w = 0; w < 3; ++w) {
                     float *S = w == 0 ? (isP ? d.ps_sum : d.cs_sum) : w == 1 ? (isP ? d.ps_sq : d.cs_sq)
                                                                             : (isP ? d.ps_vsq : d.cs_vsq);
-                    const float cs = ((colred[(0 * 3 + w) * 128 + tt] + colred[(1 * 3 + w) * 128 + tt]) +
-                                      colred[(2 * 3 + w) * 128 + tt]) + colred[(3 * 3 + w) * 128 + tt];
+                    const int wc = (!SIM_SIGMA && w == 2) ? 1 : w;  // sum of v^2 = sum of x^2 unless D2
+                    const float cs = ((colred[(0 * 3 + wc) * 128 + tt] + colred[(1 * 3 + wc) * 128 + tt]) +
+                                      colred[(2 * 3 + wc) * 128 + tt]) + colred[(3 * 3 + wc) * 128 + tt];
                     const float rs = rowred[(0 * 3 + w) * 128 + tt] + rowred[(1 * 3 + w) * 128 + tt];
                     if (bm == bn) {
                         S[(size_t)bm * ld + m0 + tt] = rs + cs;
