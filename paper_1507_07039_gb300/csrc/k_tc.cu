@@ -371,46 +371,61 @@ constexpr size_t phase2_smem()
            (P2_COLRED + P2_ROWRED) * sizeof(float) + EPI2 * P2_XPOSE * sizeof(uint16_t);
 }
 
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b)
+// hi / lo of two values at once, packed as BF16 pairs (first value in the low half)
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t &hi, uint32_t &lo)
 {
-    return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
-// 32 BF16 values held as 16 packed pairs (element 2p in the low half of p[p]).
-__device__ __forceinline__ void st32_packed(__nv_bfloat16 *dst, const uint32_t (&p)[16], uint32_t mask)
+__device__ __forceinline__ void ld16(const float *src, float (&v)[16])
 {
-    if (mask == 0xffffffffu) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            reinterpret_cast<uint4 *>(dst)[q] = make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+    for (int q = 0; q < 4; ++q) {
+        const float4 x = reinterpret_cast<const float4 *>(src)[q];
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+}
+
+// 16 BF16 values held as 8 packed pairs: two 16-byte stores, or the masked entries
+__device__ __forceinline__ void st16_packed(__nv_bfloat16 *dst, const uint32_t (&p)[8], uint32_t mask)
+{
+    if (mask == 0xffffu) {
+        reinterpret_cast<uint4 *>(dst)[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        reinterpret_cast<uint4 *>(dst)[1] = make_uint4(p[4], p[5], p[6], p[7]);
     } else {
         uint16_t *d16 = reinterpret_cast<uint16_t *>(dst);
 #pragma unroll
-        for (int q = 0; q < 32; ++q)
+        for (int q = 0; q < 16; ++q)
             if (mask >> q & 1u)
                 d16[q] = (uint16_t)(p[q >> 1] >> (16 * (q & 1)));
     }
 }
 
-// The warp's 32 x 32 block of BF16 values (row = lane, column = q, packed)
-// is written transposed: lane l stores column l as the 32 values of row
-// dst (shared memory rows of 34 halves keep both passes free of conflicts).
-__device__ __forceinline__ void store_transposed(uint16_t *xp, const uint32_t (&p)[16], __nv_bfloat16 *dst,
-                                                 uint32_t mask)
+// The warp's 32 x 16 block of BF16 values (row = lane, column = q, packed) is
+// written transposed: lane l stores row (l & 15) of the transpose, its 16
+// entries from column block (l >> 4), at dst (rows of 18 halves keep the
+// shared-memory passes free of bank conflicts).
+__device__ __forceinline__ void store_transposed16(uint16_t *xp, const uint32_t (&p)[8], __nv_bfloat16 *dst,
+                                                   uint32_t mask)
 {
     const int lane = threadIdx.x & 31;
     uint32_t *xp32 = reinterpret_cast<uint32_t *>(xp);
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-        xp32[lane * 17 + q] = p[q];
+    for (int q = 0; q < 8; ++q)
+        xp32[lane * 9 + q] = p[q];
     __syncwarp();
-    uint32_t t[16];
+    const int col = lane & 15, r0 = 16 * (lane >> 4);
+    uint32_t t[8];
 #pragma unroll
-    for (int q = 0; q < 16; ++q)
-        t[q] = (uint32_t)xp[(2 * q) * 34 + lane] | ((uint32_t)xp[(2 * q + 1) * 34 + lane] << 16);
+    for (int q = 0; q < 8; ++q)
+        t[q] = (uint32_t)xp[(r0 + 2 * q) * 18 + col] | ((uint32_t)xp[(r0 + 2 * q + 1) * 18 + col] << 16);
     __syncwarp();
     if (dst)
-        st32_packed(dst, t, mask);
+        st16_packed(dst, t, mask);
 }
 
 template <bool SIM_SIGMA>
@@ -541,31 +556,38 @@ __global__ void __launch_bounds__(THREADS2, 1)
             const int k = m0 + r, k0 = m0 + wq * 32;
             const float nk_ = k < nn ? nrm[k] : 0.0f;
             float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
+            const float *xrow = X + (size_t)k * ld + n0 + half * 64;
+            float nxt[16];
+            if (live)
+                ld16(xrow, nxt);
 #pragma unroll 1
-            for (int c = 0; c < 2 && live; ++c) {
-                const int cc = half * 2 + c, j0 = n0 + cc * 32;
+            for (int c = 0; c < 4 && live; ++c) {  // four 16-column sub-chunks of this warp's 64 columns
+                const int cc = half * 64 + c * 16, j0 = n0 + cc;
                 const size_t o = (size_t)k * ld + j0;
-                float acc[32], old[32];
-                ld32(X + o, old);                                           // global loads first,
-                const float nj = j0 + lane < nn ? nrm[j0 + lane] : 0.0f;    // column norms, one per lane,
-                tmem_ld32(sy.tmem + buf * BN + ((uint32_t)(wq * 32) << 16) + cc * 32, acc);  // then TMEM
-                if (c == 1) {  // this warp is done with the accumulator
+                float old[16], acc[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    old[q] = nxt[q];
+                if (c < 3)
+                    ld16(xrow + (c + 1) * 16, nxt);  // next sub-chunk's old values, in flight meanwhile
+                const float nj = j0 + (lane & 15) < nn ? nrm[j0 + (lane & 15)] : 0.0f;
+                tmem_ld16(sy.tmem + buf * BN + ((uint32_t)(wq * 32) << 16) + cc, acc);
+                if (c == 3) {  // this warp is done with the accumulator
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0)
                         mbar_arrive(&sy.tempty[buf]);
                 }
-                // interior chunks of off-diagonal tiles are entirely valid
-                const bool all = k < j0 && j0 + 31 < nn;
-                uint32_t vmask = 0xffffffffu;
-                if (!all) {
+                // interior sub-chunks of off-diagonal tiles are entirely valid
+                uint32_t vmask = 0xffffu;
+                if (!(k < j0 && j0 + 15 < nn)) {
                     vmask = 0;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
+                    for (int q = 0; q < 16; ++q)
                         vmask |= (k < j0 + q && j0 + q < nn) ? (1u << q) : 0u;
                 }
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
+                for (int q = 0; q < 16; ++q) {
                     const float s = tanimoto_fast(acc[q], nk_, __shfl_sync(0xffffffffu, nj, q));
                     const bool valid = (vmask >> q) & 1u;
                     const float v = valid ? fmaf(a, s, keep * old[q]) : old[q];
@@ -578,43 +600,48 @@ __global__ void __launch_bounds__(THREADS2, 1)
                     acc[q] = x;
                 }
                 // stores: FP32 upper triangle, split copies in both orientations
-                uint32_t hv[16], lv[16];
+                uint32_t hv[8], lv[8];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    __nv_bfloat16 h0, l0, h1, l1;
-                    split_bf16(old[2 * q], h0, l0);
-                    split_bf16(old[2 * q + 1], h1, l1);
-                    hv[q] = pack2(h0, h1);
-                    lv[q] = pack2(l0, l1);
-                }
-                if (vmask == 0xffffffffu) {
-                    st32(X + o, old);
+                for (int q = 0; q < 8; ++q)
+                    split_pair(old[2 * q], old[2 * q + 1], hv[q], lv[q]);
+                if (vmask == 0xffffu) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        reinterpret_cast<float4 *>(X + o)[q] =
+                            make_float4(old[4 * q], old[4 * q + 1], old[4 * q + 2], old[4 * q + 3]);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
+                    for (int q = 0; q < 16; ++q)
                         if (vmask >> q & 1u)
                             X[o + q] = old[q];
                 }
-                st32_packed(Xh + o, hv, vmask);
-                st32_packed(Xl + o, lv, vmask);
-                // mirrored entries (j, k): lane l writes row j0 + l, columns k0 .. k0 + 31
-                const int jm = j0 + lane;
-                const uint32_t mmask = jm >= nn ? 0u : (k0 + 31 < jm ? 0xffffffffu : (k0 >= jm ? 0u : ((1u << (jm - k0)) - 1u)));
-                const size_t mo = (size_t)jm * ld + k0;
-                store_transposed(xp, hv, mmask ? Xh + mo : nullptr, mmask);
-                store_transposed(xp, lv, mmask ? Xl + mo : nullptr, mmask);
+                st16_packed(Xh + o, hv, vmask);
+                st16_packed(Xl + o, lv, vmask);
+                // mirrored entries (j, k): lane l writes row j0 + (l & 15), columns k0 + 16 (l >> 4) + 0..15
+                const int jm = j0 + (lane & 15), km = k0 + 16 * (lane >> 4);
+                const uint32_t mmask =
+                    jm >= nn ? 0u : (km + 15 < jm ? 0xffffu : (km >= jm ? 0u : ((1u << (jm - km)) - 1u)));
+                const size_t mo = (size_t)jm * ld + km;
+                store_transposed16(xp, hv, mmask ? Xh + mo : nullptr, mmask);
+                store_transposed16(xp, lv, mmask ? Xl + mo : nullptr, mmask);
                 // column sums over this warp's 32 rows (x in acc; under D2 also v^2)
                 if (SIM_SIGMA) {
 #pragma unroll
-                    for (int q = 0; q < 32; ++q)
+                    for (int q = 0; q < 16; ++q)
                         old[q] = (vmask >> q & 1u) ? old[q] * old[q] : 0.0f;
-                    colred[(wq * 3 + 2) * 128 + cc * 32 + lane] = lane_transpose_sum(old);
+                    const float t2 = lane_transpose_sum16(old);
+                    if (lane < 16)
+                        colred[(wq * 3 + 2) * 128 + cc + lane] = t2;
                 }
 #pragma unroll
-                for (int q = 0; q < 32; ++q)
+                for (int q = 0; q < 16; ++q)
                     old[q] = acc[q] * acc[q];
-                colred[(wq * 3 + 1) * 128 + cc * 32 + lane] = lane_transpose_sum(old);
-                colred[(wq * 3 + 0) * 128 + cc * 32 + lane] = lane_transpose_sum(acc);
+                const float t1 = lane_transpose_sum16(old);
+                const float t0 = lane_transpose_sum16(acc);
+                if (lane < 16) {
+                    colred[(wq * 3 + 1) * 128 + cc + lane] = t1;
+                    colred[(wq * 3 + 0) * 128 + cc + lane] = t0;
+                }
             }
             if (!SIM_SIGMA)
                 rv = r2;  // x = v under rules D1 and D0

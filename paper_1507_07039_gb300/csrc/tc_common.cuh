@@ -176,6 +176,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
         v[q] = __uint_as_float(r[q]);
 }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp-collective).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q)
+        v[q] = __uint_as_float(r[q]);
+}
+
 // ---- the pipeline ------------------------------------------------------------------
 template <int STAGES>
 struct Sync {
@@ -268,6 +285,24 @@ __device__ __forceinline__ float lane_transpose_sum(float (&v)[32])
         }
     }
     return v[0];
+}
+
+// Sum v[q] (16 values) over the 32 lanes so that lanes l and l ^ 16 both end
+// with the total for q = l & 15 (16 shuffles; fixed order, so deterministic).
+__device__ __forceinline__ float lane_transpose_sum16(float (&v)[16])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 8; off >= 1; off >>= 1) {
+        const bool up = (lane & off) != 0;
+#pragma unroll
+        for (int k = 0; k < off; ++k) {
+            const float send = up ? v[k] : v[k + off];
+            const float keep = up ? v[k + off] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
