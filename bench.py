@@ -399,6 +399,44 @@ def run_ours(args, wl, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+def run_set(args, rank, world, local_rank):
+    """A set of 64 networks of uneven size (T ~ U[200, 1000], G ~ U[2000, 17000],
+    100 samples from 10 factors each), iterated together by panda_batch_run:
+    value = network-iterations/s."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_1507_07039_gb300 import panda
+    prec = {"fp32": panda.PANDA_FP32, "bf16x3": panda.PANDA_BF16X3}[args.prec]
+    wls = synth.set_of_networks(64)
+    nets = [synth.make_inputs(w) for w in wls]
+    flops = sum(algorithmic_flops(w.T, w.G) for w in wls)
+    with panda.PandaBatch(nets, prec=prec) as b:
+        del nets
+        b.run(ALPHA, 0.0, args.warmup)
+        clocks = ClockSampler(gpu_id_for(local_rank)) if rank == 0 else None
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+            time.sleep(0.6)
+        t0 = time.perf_counter()
+        conv, iters, _ = b.run(ALPHA, 0.0, args.steps)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        ck = clocks.stop() if clocks else None
+    assert all(i == args.steps for i in iters)
+    value = len(wls) * args.steps / sec
+    if rank == 0:
+        print(json.dumps({
+            "metric": "PANDA network-iterations/s over a set of networks", "value": value,
+            "unit": "network-iterations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sec / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": {0: "f32", 1: "bf16x3"}[prec], "data": "synthetic",
+            "config": {"workload": "set64", "networks": len(wls), "T": [w.T for w in wls][:8] + ["..."],
+                       "step": "one iteration of every network", "timing": "host clock between device syncs",
+                       "parallelism": "single GPU"},
+            "useful_tflops": flops * args.steps / sec / 1e12, "clocks": ck}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -416,13 +454,16 @@ def main(argv=None):
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     rank, world, local_rank = dist_env()
-    wl = synth.get(args.workload)
+    wl = synth.get(args.workload) if args.workload != "set64" else None
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
         return
     if args.prec is None:
         from paper_1507_07039_gb300 import panda
         args.prec = "bf16x3" if panda.tensor_path_available() else "fp32"
+    if args.workload == "set64":
+        run_set(args, rank, world, local_rank)
+        return
     run_ours(args, wl, rank, world, local_rank)
 
 

@@ -177,6 +177,39 @@ const char *panda_last_error(const panda_ctx *ctx);
 /* Free everything the context owns.  NULL is ignored. */
 void panda_destroy(panda_ctx *ctx);
 
+/* ---- sets of networks ----------------------------------------------------------
+ * The paper's applications compare sets of networks, one per condition or
+ * sample (Section I).  A batch holds n independent networks of their own
+ * sizes, each a context of its own (own device state and stream), created
+ * with the same options.  panda_batch_run iterates all of them at once: every
+ * network still running queues its next chunk of iterations (a captured CUDA
+ * graph) on its own stream, so small networks overlap on the GPU, and each one
+ * stops on its own h < tol (or max_iter). */
+typedef struct panda_batch panda_batch;
+
+/* T[k], G[k], W0[k], P0[k], C0[k] as in panda_create for network k (host
+ * pointers, copied).  On error nothing is kept and panda_last_error(NULL)
+ * names the failing network. */
+int panda_batch_create(panda_batch **out, int n, const int *T, const int *G, const float *const *W0,
+                       const float *const *P0, const float *const *C0, const panda_opts *o);
+
+/* Run every network until its own h < tol or max_iter iterations.
+ * iters_out[k] and h_last[k] (each may be NULL, else n entries) receive the
+ * iterations run and the last h of network k.  Returns 0 when every network
+ * converged, PANDA_NOT_CONVERGED when at least one reached max_iter. */
+int panda_batch_run(panda_batch *b, float alpha, double tol, int max_iter, int *iters_out, double *h_last);
+
+/* Network k's current W, P, C (as panda_get). */
+int panda_batch_get(panda_batch *b, int k, float *W, float *P, float *C);
+
+/* Number of networks; network k's context (owned by the batch: do not
+ * destroy it; it accepts the per-context calls such as panda_get_history). */
+int panda_batch_size(const panda_batch *b);
+panda_ctx *panda_batch_context(panda_batch *b, int k);
+
+const char *panda_batch_last_error(const panda_batch *b);
+void panda_batch_destroy(panda_batch *b);
+
 /* ---- allocation-free single iteration ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that are not allowed to allocate device memory: code running inside a host

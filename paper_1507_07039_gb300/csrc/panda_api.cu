@@ -309,67 +309,103 @@ int fill_e2(panda_ctx *c, float alpha)
     return 0;
 }
 
+// The driver, in three parts so that several contexts can run concurrently:
+// drive_begin arms the device control block for up to max_iter iterations,
+// drive_launch queues one chunk (a graph of graph_iters iterations, or that
+// many plain launches) without waiting, drive_collect waits for it and
+// reads the control block back.  Kernels of iterations past the stop do no
+// work, so a chunk never overshoots.
+struct DriveState {
+    int start = 0, before = 0;
+    bool use_graph = false;
+};
+
+int drive_begin(panda_ctx *c, float alpha, double tol, int max_iter, bool use_graph, DriveState &ds)
+{
+    int rc = fill_e2(c, alpha);
+    if (rc)
+        return rc;
+    Ctl &h = *c->h_ctl;
+    ds.start = ds.before = h.iters;
+    ds.use_graph = use_graph && c->graph_iters > 0 && c->stream != nullptr;  // the legacy NULL stream cannot be captured
+    if ((long long)ds.start + max_iter > (long long)HIST_CAP)
+        return set_err(c, PANDA_EINVAL, "iteration count would exceed the supported maximum (65536)");
+    h.active = max_iter > 0;
+    h.stop_at = ds.start + max_iter;
+    h.status = 0;
+    h.converged = 0;
+    h.alpha = alpha;
+    h.tol = tol;
+    return push_ctl(c);
+}
+
+int drive_launch(panda_ctx *c, DriveState &ds)
+{
+    Ctl &h = *c->h_ctl;
+    ds.before = h.iters;
+    const int cur = c->cur ^ ((ds.before - ds.start) & 1);
+    int rc;
+    if (ds.use_graph) {
+        if ((rc = ensure_graph(c, cur)))
+            return rc;
+        CU(cudaGraphLaunch(c->gexec[cur], c->stream));
+    } else {
+        const int K = c->graph_iters;
+        int chunk = K > 0 ? K : 1;
+        if (chunk > h.stop_at - ds.before)
+            chunk = h.stop_at - ds.before;
+        for (int k = 0; k < chunk; ++k)
+            if ((rc = launch_iteration(c, cur ^ (k & 1), k)))
+                return rc;
+    }
+    CU(cudaMemcpyAsync(c->h_ctl, c->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+    return 0;
+}
+
+// Returns 0 with *more set while the run continues.
+int drive_collect(panda_ctx *c, DriveState &ds, bool *more)
+{
+    CU(cudaStreamSynchronize(c->stream));
+    Ctl &h = *c->h_ctl;
+    if (c->prof) {  // iterations that did work in this chunk: their kernel times
+        const int nk = n_kernels(c);
+        for (int k = 0; k < h.iters - ds.before; ++k) {
+            cudaEvent_t *e = c->ev.data() + (size_t)k * (nk + 1);
+            for (int q = 0; q < nk; ++q) {
+                float ms = 0.0f;
+                CU(cudaEventElapsedTime(&ms, e[q], e[q + 1]));
+                c->k_ms[q] += ms;
+                c->k_launches[q] += 1;
+            }
+        }
+    }
+    *more = h.active != 0;
+    if (!*more) {
+        c->cur ^= ((h.iters - ds.start) & 1);
+        if (h.status & ST_NONFINITE)
+            return set_err(c, PANDA_ENONFINITE, "the state became non-finite");
+        if (h.status & ST_TIMEOUT)
+            return set_err(c, PANDA_ETIMEOUT, "a bounded device wait expired");
+    }
+    return 0;
+}
+
 // Run up to max_iter iterations (stopping early when h < tol).
 int drive(panda_ctx *c, float alpha, double tol, int max_iter, bool use_graph, int *n_done)
 {
     *n_done = 0;
     if (max_iter <= 0)
         return 0;
-    int rc = fill_e2(c, alpha);
-    if (rc)
-        return rc;
-    Ctl &h = *c->h_ctl;
-    const int start = h.iters;
-    if ((long long)start + max_iter > (long long)HIST_CAP)
-        return set_err(c, PANDA_EINVAL, "iteration count would exceed the supported maximum (65536)");
-    h.active = 1;
-    h.stop_at = start + max_iter;
-    h.status = 0;
-    h.converged = 0;
-    h.alpha = alpha;
-    h.tol = tol;
-    if ((rc = push_ctl(c)))
-        return rc;
-    const int K = c->graph_iters;
-    while (true) {
-        const int before = h.iters;
-        const int cur = c->cur ^ ((before - start) & 1);
-        if (use_graph && K > 0 && c->stream != nullptr) {  // the legacy NULL stream cannot be captured
-            if ((rc = ensure_graph(c, cur)))
-                return rc;
-            CU(cudaGraphLaunch(c->gexec[cur], c->stream));
-        } else {
-            int chunk = K > 0 ? K : 1;
-            if (chunk > h.stop_at - before)
-                chunk = h.stop_at - before;
-            for (int k = 0; k < chunk; ++k)
-                if ((rc = launch_iteration(c, cur ^ (k & 1), k)))
-                    return rc;
-        }
-        if ((rc = sync_ctl(c)))
-            return rc;
-        if (c->prof) {  // iterations that did work in this chunk: their kernel times
-            const int nk = n_kernels(c);
-            for (int k = 0; k < h.iters - before; ++k) {
-                cudaEvent_t *e = c->ev.data() + (size_t)k * (nk + 1);
-                for (int q = 0; q < nk; ++q) {
-                    float ms = 0.0f;
-                    CU(cudaEventElapsedTime(&ms, e[q], e[q + 1]));
-                    c->k_ms[q] += ms;
-                    c->k_launches[q] += 1;
-                }
-            }
-        }
-        if (!h.active)
-            break;
+    DriveState ds;
+    int rc = drive_begin(c, alpha, tol, max_iter, use_graph, ds);
+    bool more = true;
+    while (!rc && more) {
+        rc = drive_launch(c, ds);
+        if (!rc)
+            rc = drive_collect(c, ds, &more);
     }
-    *n_done = h.iters - start;
-    c->cur ^= (*n_done & 1);
-    if (h.status & ST_NONFINITE)
-        return set_err(c, PANDA_ENONFINITE, "the state became non-finite");
-    if (h.status & ST_TIMEOUT)
-        return set_err(c, PANDA_ETIMEOUT, "a bounded device wait expired");
-    return 0;
+    *n_done = c->h_ctl->iters - ds.start;
+    return rc;
 }
 
 int check_ctx(const panda_ctx *c) { return c ? 0 : PANDA_EINVAL; }
@@ -824,6 +860,117 @@ void panda_destroy(panda_ctx *c)
         return;
     free_all(c);
     delete c;
+}
+
+// ---- sets of networks ----------------------------------------------------------
+struct panda_batch {
+    std::vector<panda_ctx *> nets;
+    std::string err;
+};
+
+int panda_batch_create(panda_batch **out, int n, const int *T, const int *G, const float *const *W0,
+                       const float *const *P0, const float *const *C0, const panda_opts *o)
+{
+    if (!out)
+        return set_err(nullptr, PANDA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || !T || !G || !W0 || !P0 || !C0)
+        return set_err(nullptr, PANDA_EINVAL, "panda_batch_create: n > 0 and non-NULL arrays required");
+    panda_batch *b = new panda_batch();
+    for (int k = 0; k < n; ++k) {
+        panda_ctx *c = nullptr;
+        int rc = create_common(&c, T[k], G[k], W0[k], P0[k], C0[k], o, nullptr, false);
+        if (rc) {
+            std::string msg = "network " + std::to_string(k) + ": " + g_create_error;
+            for (panda_ctx *x : b->nets)
+                panda_destroy(x);
+            delete b;
+            return set_err(nullptr, rc, msg);
+        }
+        b->nets.push_back(c);
+    }
+    *out = b;
+    return 0;
+}
+
+int panda_batch_run(panda_batch *b, float alpha, double tol, int max_iter, int *iters_out, double *h_last)
+{
+    if (!b)
+        return PANDA_EINVAL;
+    if (!(alpha >= 0.0f && alpha <= 1.0f) || !(tol >= 0.0) || max_iter < 0) {
+        b->err = "alpha must be in [0, 1], tol >= 0 and max_iter >= 0";
+        return PANDA_EINVAL;
+    }
+    const size_t n = b->nets.size();
+    std::vector<DriveState> ds(n);
+    std::vector<char> more(n, max_iter > 0 ? 1 : 0);
+    int rc = 0;
+    for (size_t k = 0; k < n && !rc; ++k) {
+        panda_ctx *c = b->nets[k];
+        if ((rc = drive_begin(c, alpha, tol, max_iter, c->graph_iters > 0, ds[k])))
+            b->err = "network " + std::to_string(k) + ": " + c->err;
+    }
+    bool any = max_iter > 0;
+    while (!rc && any) {
+        for (size_t k = 0; k < n && !rc; ++k)  // every active network queues a chunk on its own stream
+            if (more[k] && (rc = drive_launch(b->nets[k], ds[k])))
+                b->err = "network " + std::to_string(k) + ": " + b->nets[k]->err;
+        any = false;
+        for (size_t k = 0; k < n && !rc; ++k) {
+            if (!more[k])
+                continue;
+            bool m = false;
+            if ((rc = drive_collect(b->nets[k], ds[k], &m)))
+                b->err = "network " + std::to_string(k) + ": " + b->nets[k]->err;
+            more[k] = m;
+            any = any || m;
+        }
+    }
+    if (rc) {  // leave every stream idle before reporting
+        for (panda_ctx *c : b->nets)
+            cudaStreamSynchronize(c->stream);
+        return rc;
+    }
+    bool all = true;
+    for (size_t k = 0; k < n; ++k) {
+        const Ctl &h = *b->nets[k]->h_ctl;
+        if (iters_out)
+            iters_out[k] = h.iters - ds[k].start;
+        if (h_last)
+            h_last[k] = h.h_last;
+        all = all && h.converged;
+    }
+    return all ? PANDA_OK : PANDA_NOT_CONVERGED;
+}
+
+int panda_batch_get(panda_batch *b, int k, float *W, float *P, float *C)
+{
+    if (!b || k < 0 || k >= (int)b->nets.size())
+        return PANDA_EINVAL;
+    int rc = get_impl(b->nets[k], W, P, C);
+    if (rc)
+        b->err = b->nets[k]->err;
+    return rc;
+}
+
+int panda_batch_size(const panda_batch *b) { return b ? (int)b->nets.size() : 0; }
+
+panda_ctx *panda_batch_context(panda_batch *b, int k)
+{
+    if (!b || k < 0 || k >= (int)b->nets.size())
+        return nullptr;
+    return b->nets[k];
+}
+
+const char *panda_batch_last_error(const panda_batch *b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void panda_batch_destroy(panda_batch *b)
+{
+    if (!b)
+        return;
+    for (panda_ctx *c : b->nets)
+        panda_destroy(c);
+    delete b;
 }
 
 }  // extern "C"

@@ -66,6 +66,13 @@ def _load() -> ctypes.CDLL:
         "panda_precision_supported": (i, [i]),
         "panda_step_static": (i, [i, i, vp, vp, vp, f, i, i, pd, vp]),
         "panda_selftest_tc_gemm": (i, [i, i, i, vp, vp, vp, i]),
+        "panda_batch_create": (i, [pvp, i, pi, pi, pvp, pvp, pvp, popts]),
+        "panda_batch_run": (i, [vp, f, d, i, pi, pd]),
+        "panda_batch_get": (i, [vp, i, vp, vp, vp]),
+        "panda_batch_size": (i, [vp]),
+        "panda_batch_context": (vp, [vp, i]),
+        "panda_batch_last_error": (ctypes.c_char_p, [vp]),
+        "panda_batch_destroy": (None, [vp]),
         "panda_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -329,3 +336,80 @@ class PandaContext:
             self.close()
         except Exception:
             pass
+
+
+# ---- sets of networks --------------------------------------------------------------
+
+def panda_batch_create(nets, opts: panda_opts | None = None):
+    """nets: sequence of (W0, P0, C0) host arrays; returns a batch handle."""
+    n = len(nets)
+    host = [(_host_f32(W, np.shape(W)), _host_f32(P, np.shape(P)), _host_f32(C, np.shape(C))) for W, P, C in nets]
+    T = (ctypes.c_int * n)(*[h[0].shape[0] for h in host])
+    G = (ctypes.c_int * n)(*[h[0].shape[1] for h in host])
+    ptrs = [(ctypes.c_void_p * n)(*[h[q].ctypes.data for h in host]) for q in range(3)]
+    b = ctypes.c_void_p()
+    _check(lib.panda_batch_create(ctypes.byref(b), n, T, G, ptrs[0], ptrs[1], ptrs[2],
+                                  ctypes.byref(opts) if opts is not None else None))
+    return b
+
+
+def panda_batch_run(b, alpha: float, tol: float, max_iter: int):
+    """Returns (all converged, iterations per network, last h per network)."""
+    n = lib.panda_batch_size(b)
+    iters = (ctypes.c_int * n)()
+    hl = (ctypes.c_double * n)()
+    rc = lib.panda_batch_run(b, float(alpha), float(tol), int(max_iter), iters, hl)
+    if rc < 0:
+        m = lib.panda_batch_last_error(b)
+        raise PandaError(rc, m.decode() if m else "")
+    return rc == PANDA_OK, list(iters), list(hl)
+
+
+def panda_batch_get(b, k: int, T: int, G: int):
+    W, P, C = (np.empty(s, np.float32) for s in ((T, G), (T, T), (G, G)))
+    rc = lib.panda_batch_get(b, int(k), _ptr(W), _ptr(P), _ptr(C))
+    if rc < 0:
+        m = lib.panda_batch_last_error(b)
+        raise PandaError(rc, m.decode() if m else "")
+    return W, P, C
+
+
+class PandaBatch:
+    """A set of independent networks iterated together (see panda_batch_run)."""
+
+    def __init__(self, nets, prec=PANDA_FP32, diag=PANDA_DIAG_D1, normalize=True, graph_iters=8):
+        self.shapes = [np.shape(W) for W, _, _ in nets]
+        opts = default_opts(prec=prec, diag=diag, normalize=int(bool(normalize)), graph_iters=graph_iters)
+        self.h = panda_batch_create(nets, opts)
+
+    def __len__(self):
+        return len(self.shapes)
+
+    def run(self, alpha=0.1, tol=1e-3, max_iter=200):
+        return panda_batch_run(self.h, alpha, tol, max_iter)
+
+    def get(self, k):
+        T, G = self.shapes[k]
+        return panda_batch_get(self.h, k, T, G)
+
+    def context(self, k):
+        """Network k's context handle (owned by the batch)."""
+        return ctypes.c_void_p(lib.panda_batch_context(self.h, int(k)))
+
+    def close(self):
+        if self.h:
+            lib.panda_batch_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

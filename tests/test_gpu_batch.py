@@ -1,0 +1,52 @@
+"""Sets of networks (panda_batch_*): each network of an uneven set must match
+the same network run alone (bit for bit) and the FP64 oracle (needs a GB300)."""
+from __future__ import annotations
+
+import os
+
+import numpy as np
+import pytest
+
+import gpu_helpers as gh
+from oracle.oracle import Oracle
+from paper_1507_07039_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def uneven_set(count=5, seed=77):
+    wls = synth.set_of_networks(count, seed=seed, t_range=(10, 150), g_range=(40, 400), n_samples=20,
+                                n_factors=3)
+    return [synth.make_inputs(w) for w in wls]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_matches_single_runs_and_oracle(prec):
+    from paper_1507_07039_gb300 import panda
+    nets = uneven_set()
+    with panda.PandaBatch(nets, prec=prec) as b:
+        conv, iters, hl = b.run(0.1, 1e-3, 60)
+        got = [b.get(k) for k in range(len(b))]
+        hist0 = panda.panda_get_history(b.context(0))
+    orc = Oracle()
+    orc.set_threads(os.cpu_count() or 1)
+    for k, (W0, P0, C0) in enumerate(nets):
+        single = gh.gpu_run(W0, P0, C0, prec, 0.1, 1e-3, 60)
+        assert single["iters"] == iters[k]
+        for a, g in zip((single["W"], single["P"], single["C"]), got[k]):
+            assert np.array_equal(a, g), f"network {k} differs from its single run"
+        o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, iters[k])
+        gh.assert_parity({"W": got[k][0], "P": got[k][1], "C": got[k][2]}, o, prec, f"network {k}")
+    assert hist0.size == iters[0]
+
+
+def test_batch_errors_name_the_network():
+    from paper_1507_07039_gb300 import panda
+    nets = uneven_set(3)
+    W0, P0, C0 = nets[1]
+    bad = C0.copy()
+    bad[0, 1] += 1.0
+    nets[1] = (W0, P0, bad)
+    with pytest.raises(panda.PandaError) as e:
+        panda.PandaBatch(nets)
+    assert e.value.code == -5 and "network 1" in str(e.value)
