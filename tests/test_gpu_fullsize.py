@@ -66,3 +66,25 @@ def test_human_sized_one_iteration(case, prec):
         assert abs(gC[k, k] - d) <= tol["diag"] * max(1.0, abs(d)), f"C'_{k}{k} {gC[k, k]} vs {d}"
     # properties at full size
     assert np.array_equal(gP, gP.T) and np.array_equal(gC, gC.T)
+
+
+@pytest.fixture(scope="module")
+def large_subnetwork():
+    """The large network (1600 TFs x 30000 genes, 300 samples from 30 factors)
+    restricted to the first 2000 genes of a seeded permutation: their W
+    columns and C block, all of P."""
+    from paper_1507_07039_gb300 import synth
+    wl = synth.get("large1600x30000")
+    W0, P0, C0 = synth.make_inputs(wl)
+    genes = synth.gene_subsample(wl.G, 2000, wl.seed + 99)
+    return (np.ascontiguousarray(W0[:, genes]), P0, np.ascontiguousarray(C0[np.ix_(genes, genes)]))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_large_network_gene_subsample(large_subnetwork, prec):
+    W0, P0, C0 = large_subnetwork
+    orc = Oracle()
+    orc.set_threads(os.cpu_count() or 1)
+    o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 4)
+    g = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 4)
+    gh.assert_parity(g, o, prec, "1600 x 2000 subsample")
