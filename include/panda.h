@@ -164,7 +164,9 @@ int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, do
  * computed by the same TMA + tcgen05 + TMEM machinery the BF16X3 iteration
  * uses.  A is M x K, B is N x K, D is M x N, all row-major FP32 host buffers;
  * each operand is split into BF16 hi + lo and terms = 3 sums hi*hi + hi*lo +
- * lo*hi, terms = 1 uses hi*hi only.  PANDA_EUNSUPPORTED off sm_103. */
+ * lo*hi, terms = 1 uses hi*hi only; terms + 10 runs the same product on CTA
+ * pairs (cta_group::2 MMAs over 256 x 256 tiles).  PANDA_EUNSUPPORTED off
+ * sm_103. */
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms);
 
 /* The context's stream as a cudaStream_t. */

@@ -370,7 +370,7 @@ __global__ void k_fin(Dev d)
         return;
     const int i = isP ? x : x - d.T;
     const int n = isP ? d.T : d.G;       // network size
-    const int nb = isP ? d.nbT : d.nbG;
+    const int nb = isP ? (d.nsP ? d.nsP : d.nbT) : (d.nsC ? d.nsC : d.nbG);  // partial-sum slots
     const int ld = isP ? d.Tp : d.Gp;
     const float *S1 = isP ? d.ps_sum : d.cs_sum;
     const float *S2 = isP ? d.ps_sq : d.cs_sq;

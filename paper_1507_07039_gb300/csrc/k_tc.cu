@@ -197,6 +197,119 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
+// Self-test of CTA pairs: D = A . B^T over 256 x 256 tiles, one pair of CTAs
+// per tile (cluster of 2 along x); CTA r loads A rows m0 + 128 r and B rows
+// n0 + 128 r and receives D rows m0 + 128 r .. + 127, all 256 columns.
+// ---------------------------------------------------------------------------
+constexpr int PAIR_N = 256, PAIR_ST = 3;
+constexpr uint32_t PAIR_STAGE = 4 * A_BYTES;  // per CTA: A hi, A lo, B hi, B lo (128 rows each)
+
+struct SyncPair {
+    uint64_t full[PAIR_ST], empty[PAIR_ST];
+    uint64_t accum;
+    uint32_t tmem;
+    int abort, issued, consumed;
+};
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    k_tc_selftest_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *stages = align1024(smem_raw);
+    SyncPair &sy = *reinterpret_cast<SyncPair *>(stages + PAIR_ST * PAIR_STAGE);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_ctarank();
+    const int m0 = (blockIdx.x >> 1) * 256, n0 = blockIdx.y * PAIR_N, nk = Kp / BK;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < PAIR_ST; ++q) {
+            mbar_init(&sy.full[q], 1);
+            mbar_init(&sy.empty[q], 1);
+        }
+        mbar_init(&sy.accum, 1);
+        sy.abort = 0;
+        sy.issued = 0;
+        sy.consumed = 0;
+        fence_mbar_init();
+    }
+    if (warp == 1)
+        tmem_alloc_pair(&sy.tmem, PAIR_N);
+    tc_fence_before();
+    cluster_sync();  // barriers of both CTAs initialised before any cross-CTA signal
+    tc_fence_after();
+    if (warp == 0) {
+        if (lane == 0) {  // both CTAs load their halves; completion is counted on the even CTA's barrier
+            int kb = 0;
+            for (; kb < nk; ++kb) {
+                const int s = kb % PAIR_ST;
+                const uint32_t ph = (uint32_t)(kb / PAIR_ST) & 1u;
+                if (!wait_bounded(&sy.empty[s], ph ^ 1u, &sy.abort, ctl))
+                    break;
+                const uint32_t fb = mapa_shared(smem_u32(&sy.full[s]), 0);
+                if (rank == 0)
+                    mbar_arrive_expect_tx(&sy.full[s], 2 * PAIR_STAGE);
+                uint8_t *st = stages + (size_t)s * PAIR_STAGE;
+                tma_load_2d_pair(st, &maps.Ah, fb, kb * BK, m0 + 128 * rank);
+                tma_load_2d_pair(st + A_BYTES, &maps.Al, fb, kb * BK, m0 + 128 * rank);
+                tma_load_2d_pair(st + 2 * A_BYTES, &maps.Bh, fb, kb * BK, n0 + 128 * rank);
+                tma_load_2d_pair(st + 3 * A_BYTES, &maps.Bl, fb, kb * BK, n0 + 128 * rank);
+            }
+            sy.issued = kb;
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {  // the even CTA issues the pair's MMAs
+            constexpr uint32_t idesc = idesc_bf16_f32(256, PAIR_N);
+            int kb = 0;
+            for (; kb < nk; ++kb) {
+                const int s = kb % PAIR_ST;
+                const uint32_t ph = (uint32_t)(kb / PAIR_ST) & 1u;
+                if (!wait_bounded(&sy.full[s], ph, &sy.abort, ctl))
+                    break;
+                tc_fence_after();
+                const uint32_t base = smem_u32(stages + (size_t)s * PAIR_STAGE);
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint64_t ah = sdesc_k_sw128(base + off), al = sdesc_k_sw128(base + A_BYTES + off);
+                    const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
+                    const uint64_t bl = sdesc_k_sw128(base + 3 * A_BYTES + off);
+                    mma_bf16_pair(sy.tmem, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                    mma_bf16_pair(sy.tmem, ah, bl, idesc, 1u);
+                    mma_bf16_pair(sy.tmem, al, bh, idesc, 1u);
+                }
+                mma_commit_pair(&sy.empty[s]);
+            }
+            sy.consumed = kb;
+            mma_commit_pair(&sy.accum);
+        }
+    } else {
+        const int wq = warp & 3;
+        const bool ok = wait_bounded(&sy.accum, 0, &sy.abort, ctl);
+        tc_fence_after();
+        if (ok && !*(volatile int *)&sy.abort) {
+            const int r = m0 + 128 * rank + wq * 32 + lane;
+            const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
+#pragma unroll 1
+            for (int c = 0; c < PAIR_N / 32; ++c) {
+                float v[32];
+                tmem_ld32(trow + c * 32, v);
+                st32(D + (size_t)r * Np + n0 + c * 32, v);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && rank == 0)  // loads counted here but not consumed (abort only)
+        for (int kb = sy.consumed; kb < sy.consumed + PAIR_ST && kb < nk; ++kb)
+            if (kb < sy.issued)
+                wait_bounded(&sy.full[kb % PAIR_ST], (uint32_t)(kb / PAIR_ST) & 1u, &sy.abort, ctl, true);
+    cluster_sync();  // neither CTA leaves while the pair may still signal it
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(sy.tmem, PAIR_N);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Phase 1 (grid: x = T tile of 128, y = G tile of BN1)
 // ---------------------------------------------------------------------------
 constexpr size_t phase1_smem()
@@ -344,26 +457,35 @@ __global__ void __launch_bounds__(THREADS, 1) k_tc_phase1(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------
-// Phase 2: persistent CTAs over a host-built schedule of upper-triangle
-// 128 x 128 tiles of W'.W'^T (P, K = genes) and W'^T.W' (C, K = TFs).  Two
-// TMEM accumulators alternate, so the epilogue of one tile overlaps the MMAs
-// of the next.  Warps: 0 TMA, 1 MMA, 2-9 epilogue (two per TMEM lane quarter,
-// each taking 64 of the 128 columns).
+// Phase 2: persistent CTA pairs over a host-built schedule of upper-triangle
+// 256 x 256 tiles of W'.W'^T (P, K = genes) and W'^T.W' (C, K = TFs).  In a
+// pair, CTA r loads rows 128 r .. 128 r + 127 of the tile's A and B blocks;
+// the even CTA issues cta_group::2 MMAs (M = N = 256) whose result rows
+// 128 r .. + 127 land in CTA r's TMEM.  Two accumulators of 256 columns
+// alternate, so the epilogue of one tile overlaps the MMAs of the next.
+// Warps: 0 TMA, 1 MMA (even CTA), 2-9 epilogue (two per TMEM lane quarter,
+// each taking 128 of the 256 columns in 16-column sub-chunks).
+//
+// Row partial sums for Eq. 6 use separate slot ranges so the two CTAs of a
+// pair never exchange data: the row role (a row of the tile, summed over its
+// 256 columns) goes to slot bn, the column role (a column of the tile, summed
+// over this CTA's 128 rows) to slot nb + 2 bm + r.
 // ---------------------------------------------------------------------------
 constexpr int EPI2 = 8;
 constexpr int THREADS2 = 64 + 32 * EPI2;
-constexpr uint32_t STAGE2 = 4 * A_BYTES;  // A hi, A lo, B hi, B lo (B is 128 rows too)
+constexpr int N2 = 256;                    // tile edge
+constexpr uint32_t STAGE2 = 4 * A_BYTES;   // per CTA: A hi, A lo, B hi, B lo (128 rows each)
 
 struct Sync2 {
     uint64_t full[ST2], empty[ST2];
-    uint64_t tfull[2], tempty[2];  // accumulator ready / accumulator drained
+    uint64_t tfull[2], tempty[2];  // accumulator ready / accumulator drained (by both CTAs)
     uint32_t tmem;
     int abort, issued, consumed;
 };
 
-constexpr size_t P2_COLRED = 4 * 3 * 128;  // [quarter][sum][column] floats
+constexpr size_t P2_COLRED = 4 * 3 * N2;   // [quarter][sum][column] floats
 constexpr size_t P2_ROWRED = 2 * 3 * 128;  // [half][sum][row] floats
-constexpr size_t P2_XPOSE = 32 * 34;       // per epilogue warp, uint16
+constexpr size_t P2_XPOSE = 32 * 18;       // per epilogue warp, uint16
 
 constexpr size_t phase2_smem()
 {
@@ -429,15 +551,13 @@ __device__ __forceinline__ void store_transposed16(uint16_t *xp, const uint32_t 
 }
 
 template <bool SIM_SIGMA>
-__global__ void __launch_bounds__(THREADS2, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
     k_tc_phase2(const __grid_constant__ TcMaps maps, Dev d, int cur, const int *__restrict__ sched_off,
                 const int *__restrict__ sched)
 {
     Ctl *ctl = d.ctl;
-    if (!ctl->active)
+    if (!ctl->active)  // both CTAs of a pair see the same value and leave together
         return;
-    constexpr int BN = 128;
-    constexpr uint32_t B_BYTES = BN * BK * 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
     Sync2 &sy = *reinterpret_cast<Sync2 *>(stages + ST2 * STAGE2);
@@ -446,7 +566,9 @@ __global__ void __launch_bounds__(THREADS2, 1)
     uint16_t *xpose = reinterpret_cast<uint16_t *>(rowred + P2_ROWRED);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int first = sched_off[blockIdx.x], last = sched_off[blockIdx.x + 1];
+    const uint32_t rank = cluster_ctarank();
+    const int pair = blockIdx.x >> 1;
+    const int first = sched_off[pair], last = sched_off[pair + 1];
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < ST2; ++q) {
@@ -455,7 +577,7 @@ __global__ void __launch_bounds__(THREADS2, 1)
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(&sy.tfull[q], 1);
-            mbar_init(&sy.tempty[q], EPI2);
+            mbar_init(&sy.tempty[q], 2 * EPI2);
         }
         sy.abort = 0;
         sy.issued = 0;
@@ -463,19 +585,19 @@ __global__ void __launch_bounds__(THREADS2, 1)
         fence_mbar_init();
     }
     if (warp == 1)
-        tmem_alloc(&sy.tmem, 2 * BN);
+        tmem_alloc_pair(&sy.tmem, 2 * N2);
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();  // both CTAs' barriers exist before any cross-CTA signal
     tc_fence_after();
 
     if (warp == 0) {
-        if (lane == 0) {  // ---- TMA producer ----
+        if (lane == 0) {  // ---- TMA producer (both CTAs; completion counted on the even CTA) ----
             int g = 0;
             bool ok = true;
             for (int n = first; n < last && ok; ++n) {
                 const int tile = sched[n];
                 const bool isP = tile < 0;
-                const int m0 = ((tile >> 16) & 0x7fff) * BM, n0 = (tile & 0xffff) * BN;
+                const int m0 = ((tile >> 16) & 0x7fff) * N2 + 128 * rank, n0 = (tile & 0xffff) * N2 + 128 * rank;
                 const int nk = (isP ? d.Gp : d.Tp) / BK;
                 const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Wth2[cur];
                 const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl2[cur];
@@ -485,19 +607,21 @@ __global__ void __launch_bounds__(THREADS2, 1)
                         ok = false;
                         break;
                     }
+                    const uint32_t fb = mapa_shared(smem_u32(&sy.full[st]), 0);
+                    if (rank == 0)
+                        mbar_arrive_expect_tx(&sy.full[st], 2 * STAGE2);
                     uint8_t *b = stages + (size_t)st * STAGE2;
-                    mbar_arrive_expect_tx(&sy.full[st], STAGE2);
-                    tma_load_2d(b, mh, &sy.full[st], kb * BK, m0);
-                    tma_load_2d(b + A_BYTES, ml, &sy.full[st], kb * BK, m0);
-                    tma_load_2d(b + 2 * A_BYTES, mh, &sy.full[st], kb * BK, n0);
-                    tma_load_2d(b + 2 * A_BYTES + B_BYTES, ml, &sy.full[st], kb * BK, n0);
+                    tma_load_2d_pair(b, mh, fb, kb * BK, m0);
+                    tma_load_2d_pair(b + A_BYTES, ml, fb, kb * BK, m0);
+                    tma_load_2d_pair(b + 2 * A_BYTES, mh, fb, kb * BK, n0);
+                    tma_load_2d_pair(b + 3 * A_BYTES, ml, fb, kb * BK, n0);
                 }
             }
             sy.issued = g;
         }
     } else if (warp == 1) {
-        if (lane == 0) {  // ---- MMA issuer ----
-            constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+        if (lane == 0 && rank == 0) {  // ---- MMA issuer of the pair ----
+            constexpr uint32_t idesc = idesc_bf16_f32(256, N2);
             int g = 0;
             bool ok = true;
             for (int n = first, idx = 0; n < last && ok; ++n, ++idx) {
@@ -507,7 +631,7 @@ __global__ void __launch_bounds__(THREADS2, 1)
                 if (!wait_bounded(&sy.tempty[buf], ((uint32_t)(idx >> 1) & 1u) ^ 1u, &sy.abort, ctl))
                     break;
                 tc_fence_after();
-                const uint32_t dacc = sy.tmem + buf * BN;
+                const uint32_t dacc = sy.tmem + buf * N2;
                 for (int kb = 0; kb < nk; ++kb, ++g) {
                     const int st = g % ST2;
                     if (!wait_bounded(&sy.full[st], (uint32_t)(g / ST2) & 1u, &sy.abort, ctl)) {
@@ -522,29 +646,31 @@ __global__ void __launch_bounds__(THREADS2, 1)
                         const uint64_t ah = sdesc_k_sw128(base + off);
                         const uint64_t al = sdesc_k_sw128(base + A_BYTES + off);
                         const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
-                        const uint64_t bl = sdesc_k_sw128(base + 2 * A_BYTES + B_BYTES + off);
-                        mma_bf16(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
-                        mma_bf16(dacc, ah, bl, idesc, 1u);
-                        mma_bf16(dacc, al, bh, idesc, 1u);
+                        const uint64_t bl = sdesc_k_sw128(base + 3 * A_BYTES + off);
+                        mma_bf16_pair(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                        mma_bf16_pair(dacc, ah, bl, idesc, 1u);
+                        mma_bf16_pair(dacc, al, bh, idesc, 1u);
                     }
-                    mma_commit(&sy.empty[st]);
+                    mma_commit_pair(&sy.empty[st]);
                 }
-                mma_commit(&sy.tfull[buf]);
+                mma_commit_pair(&sy.tfull[buf]);
             }
             sy.consumed = g;
         }
-    } else {  // ---- epilogue: warps 2..9 ----
+    } else {  // ---- epilogue: warps 2..9 of both CTAs ----
         const int e = warp - 2, wq = warp & 3, half = e >> 2;
-        const int r = wq * 32 + lane;
+        const int r = wq * 32 + lane;  // row of this CTA's 128-row half
         uint16_t *xp = xpose + (size_t)e * P2_XPOSE;
         const int tt = threadIdx.x - 64;  // 0..255
         const float a = ctl->alpha, keep = 1.0f - a;
+        const uint32_t tempty_even = mapa_shared(smem_u32(&sy.tempty[0]), 0);
         for (int n = first, idx = 0; n < last; ++n, ++idx) {
             const int tile = sched[n];
             const bool isP = tile < 0;
             const int bm = (tile >> 16) & 0x7fff, bn = tile & 0xffff;
-            const int m0 = bm * BM, n0 = bn * BN;
+            const int m0 = bm * N2 + 128 * (int)rank, n0 = bn * N2;
             const int nn = isP ? d.T : d.G, ld = isP ? d.Tp : d.Gp;
+            const int nbk = ceil_div(ld, N2);  // 256-blocks: the column-role slots start here
             const float *nrm = isP ? d.rsqW : d.csqW;
             float *X = isP ? d.Poff : d.Coff;
             __nv_bfloat16 *Xh = isP ? d.Ph : d.Ch, *Xl = isP ? d.Pl : d.Cl;
@@ -554,29 +680,31 @@ __global__ void __launch_bounds__(THREADS2, 1)
                               !*(volatile int *)&sy.abort;
             tc_fence_after();
             const int k = m0 + r, k0 = m0 + wq * 32;
-            const float nk_ = k < nn ? nrm[k] : 0.0f;
+            const bool krow = k < nn;  // rows past the network (last block's padding) hold nothing
+            const float nk_ = krow ? nrm[k] : 0.0f;
             float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
-            const float *xrow = X + (size_t)k * ld + n0 + half * 64;
+            const float *xrow = X + (size_t)(krow ? k : 0) * ld + n0 + half * 128;
             float nxt[16];
-            if (live)
+            if (live && krow && n0 + half * 128 < ld)
                 ld16(xrow, nxt);
 #pragma unroll 1
-            for (int c = 0; c < 4 && live; ++c) {  // four 16-column sub-chunks of this warp's 64 columns
-                const int cc = half * 64 + c * 16, j0 = n0 + cc;
+            for (int c = 0; c < 8 && live; ++c) {  // eight 16-column sub-chunks of this warp's 128 columns
+                const int cc = half * 128 + c * 16, j0 = n0 + cc;
                 const size_t o = (size_t)k * ld + j0;
+                const bool inside = krow && j0 < ld;
                 float old[16], acc[16];
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    old[q] = nxt[q];
-                if (c < 3)
+                    old[q] = inside ? nxt[q] : 0.0f;
+                if (c < 7 && krow && j0 + 16 < ld)
                     ld16(xrow + (c + 1) * 16, nxt);  // next sub-chunk's old values, in flight meanwhile
                 const float nj = j0 + (lane & 15) < nn ? nrm[j0 + (lane & 15)] : 0.0f;
-                tmem_ld16(sy.tmem + buf * BN + ((uint32_t)(wq * 32) << 16) + cc, acc);
-                if (c == 3) {  // this warp is done with the accumulator
+                tmem_ld16(sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16) + cc, acc);
+                if (c == 7) {  // this warp is done with the accumulator: tell the even CTA
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0)
-                        mbar_arrive(&sy.tempty[buf]);
+                        mbar_arrive_cluster(tempty_even + buf * (uint32_t)sizeof(uint64_t));
                 }
                 // interior sub-chunks of off-diagonal tiles are entirely valid
                 uint32_t vmask = 0xffffu;
@@ -609,14 +737,16 @@ __global__ void __launch_bounds__(THREADS2, 1)
                     for (int q = 0; q < 4; ++q)
                         reinterpret_cast<float4 *>(X + o)[q] =
                             make_float4(old[4 * q], old[4 * q + 1], old[4 * q + 2], old[4 * q + 3]);
-                } else {
+                } else if (vmask) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
                         if (vmask >> q & 1u)
                             X[o + q] = old[q];
                 }
-                st16_packed(Xh + o, hv, vmask);
-                st16_packed(Xl + o, lv, vmask);
+                if (vmask) {
+                    st16_packed(Xh + o, hv, vmask);
+                    st16_packed(Xl + o, lv, vmask);
+                }
                 // mirrored entries (j, k): lane l writes row j0 + (l & 15), columns k0 + 16 (l >> 4) + 0..15
                 const int jm = j0 + (lane & 15), km = k0 + 16 * (lane >> 4);
                 const uint32_t mmask =
@@ -631,7 +761,7 @@ __global__ void __launch_bounds__(THREADS2, 1)
                         old[q] = (vmask >> q & 1u) ? old[q] * old[q] : 0.0f;
                     const float t2 = lane_transpose_sum16(old);
                     if (lane < 16)
-                        colred[(wq * 3 + 2) * 128 + cc + lane] = t2;
+                        colred[(wq * 3 + 2) * N2 + cc + lane] = t2;
                 }
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
@@ -639,8 +769,8 @@ __global__ void __launch_bounds__(THREADS2, 1)
                 const float t1 = lane_transpose_sum16(old);
                 const float t0 = lane_transpose_sum16(acc);
                 if (lane < 16) {
-                    colred[(wq * 3 + 1) * 128 + cc + lane] = t1;
-                    colred[(wq * 3 + 0) * 128 + cc + lane] = t0;
+                    colred[(wq * 3 + 1) * N2 + cc + lane] = t1;
+                    colred[(wq * 3 + 0) * N2 + cc + lane] = t0;
                 }
             }
             if (!SIM_SIGMA)
@@ -649,21 +779,20 @@ __global__ void __launch_bounds__(THREADS2, 1)
             rowred[(half * 3 + 1) * 128 + r] = r2;
             rowred[(half * 3 + 2) * 128 + r] = rv;
             epi_bar2();
-            if (tt < 128 && live) {
+            if (live) {
 #pragma unroll
                 for (int w = 0; w < 3; ++w) {
                     float *S = w == 0 ? (isP ? d.ps_sum : d.cs_sum) : w == 1 ? (isP ? d.ps_sq : d.cs_sq)
                                                                             : (isP ? d.ps_vsq : d.cs_vsq);
                     const int wc = (!SIM_SIGMA && w == 2) ? 1 : w;  // sum of v^2 = sum of x^2 unless D2
-                    const float cs = ((colred[(0 * 3 + wc) * 128 + tt] + colred[(1 * 3 + wc) * 128 + tt]) +
-                                      colred[(2 * 3 + wc) * 128 + tt]) + colred[(3 * 3 + wc) * 128 + tt];
-                    const float rs = rowred[(0 * 3 + w) * 128 + tt] + rowred[(1 * 3 + w) * 128 + tt];
-                    if (bm == bn) {
-                        S[(size_t)bm * ld + m0 + tt] = rs + cs;
-                    } else {
-                        S[(size_t)bn * ld + m0 + tt] = rs;  // rows of this tile, slot of its column block
-                        S[(size_t)bm * ld + n0 + tt] = cs;  // mirrored rows, slot of its row block
-                    }
+                    // column role: tile column tt, summed over this CTA's 128 rows
+                    const float cs = ((colred[(0 * 3 + wc) * N2 + tt] + colred[(1 * 3 + wc) * N2 + tt]) +
+                                      colred[(2 * 3 + wc) * N2 + tt]) + colred[(3 * 3 + wc) * N2 + tt];
+                    if (n0 + tt < ld)
+                        S[(size_t)(nbk + 2 * bm + (int)rank) * ld + n0 + tt] = cs;
+                    // row role: tile row tt of this CTA, summed over the 256 columns
+                    if (tt < 128 && m0 + tt < ld)
+                        S[(size_t)bn * ld + m0 + tt] = rowred[(0 * 3 + w) * 128 + tt] + rowred[(1 * 3 + w) * 128 + tt];
                 }
             }
             epi_bar2();
@@ -671,14 +800,13 @@ __global__ void __launch_bounds__(THREADS2, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0) {  // drain: loads issued but not consumed, and the last MMAs
-        for (int g = sy.consumed; g < sy.issued; ++g)
+    if (threadIdx.x == 0 && rank == 0)  // loads counted here but not consumed (abort only)
+        for (int g = sy.consumed; g < sy.consumed + ST2 && g < sy.issued; ++g)
             wait_bounded(&sy.full[g % ST2], (uint32_t)(g / ST2) & 1u, &sy.abort, ctl, true);
-    }
-    __syncthreads();
+    cluster_sync();  // neither CTA leaves while the pair may still signal it
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(sy.tmem, 2 * BN);
+        tmem_dealloc_pair(sy.tmem, 2 * N2);
     }
 }
 
@@ -716,6 +844,8 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int rows, int cols, int b
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+constexpr size_t pair_smem() { return 1024 + (size_t)PAIR_ST * PAIR_STAGE + sizeof(SyncPair) + 16; }
+
 struct TcHost {
     TcMaps maps;
     int *sched_off = nullptr;  // [grid2 + 1] offsets into sched
@@ -723,18 +853,20 @@ struct TcHost {
     int grid2 = 0;
 };
 
-// Longest-processing-time assignment of the upper-triangle tiles of P and C to
-// `ctas` persistent CTAs; cost of a tile = its k-blocks + a fixed epilogue share.
+// Longest-processing-time assignment of the upper-triangle 256 x 256 tiles of
+// P and C to `ctas` persistent CTA pairs; cost of a tile = its k-blocks + a
+// fixed epilogue share.
 void build_schedule(const Dev &d, int ctas, std::vector<int> &off, std::vector<int> &tiles)
 {
     struct T_ { int cost, code; };
     std::vector<T_> all;
-    const int kP = d.Gp / BK, kC = d.Tp / BK, epi = 8;
-    for (int bm = 0; bm < d.nbT; ++bm)
-        for (int bn = bm; bn < d.nbT; ++bn)
+    const int kP = d.Gp / BK, kC = d.Tp / BK, epi = 16;
+    const int nbP = ceil_div(d.Tp, N2), nbC = ceil_div(d.Gp, N2);
+    for (int bm = 0; bm < nbP; ++bm)
+        for (int bn = bm; bn < nbP; ++bn)
             all.push_back({kP + epi, (int)(0x80000000u | ((uint32_t)bm << 16) | (uint32_t)bn)});
-    for (int bm = 0; bm < d.nbG; ++bm)
-        for (int bn = bm; bn < d.nbG; ++bn)
+    for (int bm = 0; bm < nbC; ++bm)
+        for (int bn = bm; bn < nbC; ++bn)
             all.push_back({kC + epi, (bm << 16) | bn});
     std::stable_sort(all.begin(), all.end(), [](const T_ &a, const T_ &b) { return a.cost > b.cost; });
     if (ctas > (int)all.size())
@@ -774,6 +906,9 @@ cudaError_t set_smem_limits()
         return e;
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
     if ((e = cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_tc_selftest_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)pair_smem())))
         return e;
     done = true;
     return cudaSuccess;
@@ -827,8 +962,8 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s)
         if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
             return e;
         std::vector<int> off, tiles;
-        build_schedule(d, nsm, off, tiles);
-        h->grid2 = (int)off.size() - 1;
+        build_schedule(d, nsm / 2, off, tiles);  // one list per CTA pair
+        h->grid2 = 2 * ((int)off.size() - 1);
         if ((e = cudaMalloc(&h->sched_off, off.size() * sizeof(int))) ||
             (e = cudaMalloc(&h->sched, tiles.size() * sizeof(int))) ||
             (e = cudaMemcpy(h->sched_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
@@ -871,12 +1006,12 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
 
 // D = A . B^T on the tensor-core pipeline (self-test support)
 cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms,
-                             int *status)
+                             int pair, int *status)
 {
     cudaError_t e = set_smem_limits();
     if (e)
         return e;
-    const int Mp = round_up(M, 128), Np = round_up(N, 128), Kp = round_up(K, 64);
+    const int Mp = round_up(M, pair ? 256 : 128), Np = round_up(N, pair ? PAIR_N : 128), Kp = round_up(K, 64);
     float *dA = nullptr, *dB = nullptr, *dD = nullptr;
     __nv_bfloat16 *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
     Ctl *ctl = nullptr;
@@ -915,7 +1050,10 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     TRY(make_map(&maps.Bh, Bh, Np, Kp, 128));
     TRY(make_map(&maps.Bl, Bl, Np, Kp, 128));
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
-    k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl);
+    if (pair)
+        k_tc_selftest_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl);
+    else
+        k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl);
     TRY(cudaGetLastError());
     TRY(cudaDeviceSynchronize());
     Ctl h;

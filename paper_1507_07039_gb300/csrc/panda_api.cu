@@ -129,12 +129,17 @@ int plan_memory(panda_ctx *c)
     DALLOC(d.wrow_part, (size_t)c->nbG * Tp);
     DALLOC(d.wcol_part, (size_t)c->nbT * Gp);
     DALLOC(d.hpart, (size_t)c->nbT * c->nbG);
-    DALLOC(d.ps_sum, (size_t)c->nbT * Tp);
-    DALLOC(d.ps_sq, (size_t)c->nbT * Tp);
-    DALLOC(d.ps_vsq, (size_t)c->nbT * Tp);
-    DALLOC(d.cs_sum, (size_t)c->nbG * Gp);
-    DALLOC(d.cs_sq, (size_t)c->nbG * Gp);
-    DALLOC(d.cs_vsq, (size_t)c->nbG * Gp);
+    // partial-sum slots: one per 128-row block (FP32 path); on the tensor-core
+    // path one per 256-column block for the row role plus one per 128-row half
+    // for the column role (see k_tc.cu)
+    d.nsP = c->prec == PANDA_BF16X3 ? 3 * ceil_div(c->Tp, 256) : c->nbT;
+    d.nsC = c->prec == PANDA_BF16X3 ? 3 * ceil_div(c->Gp, 256) : c->nbG;
+    DALLOC(d.ps_sum, (size_t)d.nsP * Tp);
+    DALLOC(d.ps_sq, (size_t)d.nsP * Tp);
+    DALLOC(d.ps_vsq, (size_t)d.nsP * Tp);
+    DALLOC(d.cs_sum, (size_t)d.nsC * Gp);
+    DALLOC(d.cs_sq, (size_t)d.nsC * Gp);
+    DALLOC(d.cs_vsq, (size_t)d.nsC * Gp);
     DALLOC(d.ctl, 1);
     DALLOC(d.hist, HIST_CAP);
     DALLOC(d.e2tab, HIST_CAP + 1);
@@ -821,12 +826,15 @@ int panda_kernel_count(const panda_ctx *c) { return c ? n_kernels(c) : 0; }
 
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms)
 {
+    // terms + 10: the same product on CTA pairs (cta_group::2, 256 x 256 tiles)
+    const int pair = terms >= 10;
+    terms %= 10;
     if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !D || (terms != 1 && terms != 3))
         return set_err(nullptr, PANDA_EINVAL, "panda_selftest_tc_gemm: bad argument");
     if (!tc_supported())
         return set_err(nullptr, PANDA_EUNSUPPORTED, "panda_selftest_tc_gemm: needs an sm_103 device");
     int status = 0;
-    cudaError_t e = tc_selftest_gemm(M, N, K, A, B, D, terms, &status);
+    cudaError_t e = tc_selftest_gemm(M, N, K, A, B, D, terms, pair, &status);
     if (e != cudaSuccess)
         return set_err(nullptr, PANDA_ECUDA, std::string("panda_selftest_tc_gemm: ") + cudaGetErrorString(e));
     if (status & ST_TIMEOUT)

@@ -51,8 +51,9 @@ struct Dev {
     float *wrow_part;            // nbG x Tp
     float *wcol_part;            // nbT x Gp
     double *hpart;               // nbT * nbG
-    float *ps_sum, *ps_sq, *ps_vsq;  // nbT x Tp  row partials of P'
-    float *cs_sum, *cs_sq, *cs_vsq;  // nbG x Gp  row partials of C'
+    float *ps_sum, *ps_sq, *ps_vsq;  // nsP x Tp  row partials of P'
+    float *cs_sum, *cs_sq, *cs_vsq;  // nsC x Gp  row partials of C'
+    int nsP, nsC;                    // partial-sum slots per row (0: one per 128-row block)
     Ctl *ctl;
     double *hist;                // HIST_CAP
     double *e2tab;               // HIST_CAP + 1: e^{2 alpha t}, computed on the host
@@ -120,6 +121,6 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
 // D (M x N, row-major) = A (M x K) . B (N x K)^T through the tcgen05 pipeline,
 // host buffers; terms = 1 (hi only) or 3 (split).  *status: device status bits.
 cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms,
-                             int *status);
+                             int pair, int *status);
 
 }  // namespace panda

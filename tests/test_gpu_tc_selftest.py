@@ -48,3 +48,21 @@ def test_three_term_split_product(M, N, K):
     assert np.max(np.abs(D - ref3)) / scale < 1e-5
     # plus the dropped lo*lo term and the split residuals (below 2^-16 relative per product)
     assert np.max(np.abs(D - exact)) / scale < 3e-5
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (300, 600, 1000), (512, 256, 130)])
+def test_cta_pair_product(M, N, K):
+    """The same product on CTA pairs (cta_group::2 MMAs over 256 x 256 tiles)."""
+    from paper_1507_07039_gb300 import panda
+    rng = np.random.default_rng(3 * M + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    D1 = panda.panda_selftest_tc_gemm(A, B, terms=11)
+    Ah, Al = bf16_split(A)
+    Bh, Bl = bf16_split(B)
+    ref1 = Ah @ Bh.T
+    scale = max(1.0, np.max(np.abs(ref1)))
+    assert np.max(np.abs(D1 - ref1)) / scale < 2e-6
+    D3 = panda.panda_selftest_tc_gemm(A, B, terms=13)
+    ref3 = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
+    assert np.max(np.abs(D3 - ref3)) / scale < 1e-5
