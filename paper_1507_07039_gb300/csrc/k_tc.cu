@@ -40,7 +40,6 @@ using namespace tc;
 
 constexpr int BN1 = 256;     // phase-1 tile width (genes)
 constexpr int ST1 = 2;       // phase-1 pipeline stages (96 KB each)
-constexpr int ST2 = 3;       // phase-2 pipeline stages (64 KB each)
 
 struct TcMaps {
     CUtensorMap Ph, Pl;              // P_off split   [Tp][Tp]  box 64 x 128
@@ -77,17 +76,6 @@ __global__ void k_split(const float *__restrict__ X, size_t n, __nv_bfloat16 *__
 {
     for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
         split_bf16(X[q], H[q], L[q]);
-}
-
-__device__ __forceinline__ void tri_decode(int u, int nb, int &bm, int &bn)
-{
-    int r = 0;
-    while (u >= nb - r) {
-        u -= nb - r;
-        ++r;
-    }
-    bm = r;
-    bn = r + u;
 }
 
 template <int STAGES>
@@ -476,21 +464,32 @@ constexpr int THREADS2 = 64 + 32 * EPI2;
 constexpr int N2 = 256;                    // tile edge
 constexpr uint32_t STAGE2 = 4 * A_BYTES;   // per CTA: A hi, A lo, B hi, B lo (128 rows each)
 
-struct Sync2 {
-    uint64_t full[ST2], empty[ST2];
+// Rule D2 keeps three partial sums per row instead of two and so runs with one
+// stage fewer to fit its larger reduction buffers.
+template <bool SIM>
+struct P2Cfg {
+    static constexpr int NS = SIM ? 3 : 2;             // sums per row: x, x^2 (and v^2 under D2)
+    static constexpr int ST = SIM ? 2 : 3;             // pipeline stages
+    static constexpr size_t COLRED = 4 * NS * N2;      // [quarter][sum][column] floats
+    static constexpr size_t ROWRED = 2 * NS * 128;     // [half][sum][row] floats
+    static constexpr size_t COLNRM = N2;               // the tile's column norms
+    static constexpr size_t BLK = 32 * 17;             // per epilogue warp: 32 x 16 staging block (padded)
+};
+
+template <int ST>
+struct Sync2T {
+    uint64_t full[ST], empty[ST];
     uint64_t tfull[2], tempty[2];  // accumulator ready / accumulator drained (by both CTAs)
     uint32_t tmem;
     int abort, issued, consumed;
 };
 
-constexpr size_t P2_COLRED = 4 * 3 * N2;   // [quarter][sum][column] floats
-constexpr size_t P2_ROWRED = 2 * 3 * 128;  // [half][sum][row] floats
-constexpr size_t P2_XPOSE = 32 * 18;       // per epilogue warp, uint16
-
+template <bool SIM>
 constexpr size_t phase2_smem()
 {
-    return 1024 + (size_t)ST2 * STAGE2 + ((sizeof(Sync2) + 15) & ~size_t(15)) +
-           (P2_COLRED + P2_ROWRED) * sizeof(float) + EPI2 * P2_XPOSE * sizeof(uint16_t);
+    using C = P2Cfg<SIM>;
+    return 1024 + (size_t)C::ST * STAGE2 + ((sizeof(Sync2T<C::ST>) + 15) & ~size_t(15)) +
+           (C::COLRED + C::ROWRED + C::COLNRM + EPI2 * C::BLK) * sizeof(float);
 }
 
 // hi / lo of two values at once, packed as BF16 pairs (first value in the low half)
@@ -527,29 +526,6 @@ __device__ __forceinline__ void st16_packed(__nv_bfloat16 *dst, const uint32_t (
     }
 }
 
-// The warp's 32 x 16 block of BF16 values (row = lane, column = q, packed) is
-// written transposed: lane l stores row (l & 15) of the transpose, its 16
-// entries from column block (l >> 4), at dst (rows of 18 halves keep the
-// shared-memory passes free of bank conflicts).
-__device__ __forceinline__ void store_transposed16(uint16_t *xp, const uint32_t (&p)[8], __nv_bfloat16 *dst,
-                                                   uint32_t mask)
-{
-    const int lane = threadIdx.x & 31;
-    uint32_t *xp32 = reinterpret_cast<uint32_t *>(xp);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        xp32[lane * 9 + q] = p[q];
-    __syncwarp();
-    const int col = lane & 15, r0 = 16 * (lane >> 4);
-    uint32_t t[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        t[q] = (uint32_t)xp[(r0 + 2 * q) * 18 + col] | ((uint32_t)xp[(r0 + 2 * q + 1) * 18 + col] << 16);
-    __syncwarp();
-    if (dst)
-        st16_packed(dst, t, mask);
-}
-
 template <bool SIM_SIGMA>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
     k_tc_phase2(const __grid_constant__ TcMaps maps, Dev d, int cur, const int *__restrict__ sched_off,
@@ -558,12 +534,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
     Ctl *ctl = d.ctl;
     if (!ctl->active)  // both CTAs of a pair see the same value and leave together
         return;
+    using Cfg = P2Cfg<SIM_SIGMA>;
+    constexpr int ST2 = Cfg::ST, NS = Cfg::NS;
+    using Sync2 = Sync2T<ST2>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
     Sync2 &sy = *reinterpret_cast<Sync2 *>(stages + ST2 * STAGE2);
     float *colred = reinterpret_cast<float *>(stages + ST2 * STAGE2 + ((sizeof(Sync2) + 15) & ~size_t(15)));
-    float *rowred = colred + P2_COLRED;
-    uint16_t *xpose = reinterpret_cast<uint16_t *>(rowred + P2_ROWRED);
+    float *rowred = colred + Cfg::COLRED;
+    float *colnrm = rowred + Cfg::ROWRED;
+    float *blocks = colnrm + Cfg::COLNRM;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
@@ -660,7 +640,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
     } else {  // ---- epilogue: warps 2..9 of both CTAs ----
         const int e = warp - 2, wq = warp & 3, half = e >> 2;
         const int r = wq * 32 + lane;  // row of this CTA's 128-row half
-        uint16_t *xp = xpose + (size_t)e * P2_XPOSE;
+        float *blk = blocks + (size_t)e * Cfg::BLK;  // this warp's 32 x 16 staging block, rows of 17
         const int tt = threadIdx.x - 64;  // 0..255
         const float a = ctl->alpha, keep = 1.0f - a;
         const uint32_t tempty_even = mapa_shared(smem_u32(&sy.tempty[0]), 0);
@@ -675,22 +655,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             float *X = isP ? d.Poff : d.Coff;
             __nv_bfloat16 *Xh = isP ? d.Ph : d.Ch, *Xl = isP ? d.Pl : d.Cl;
             const int buf = idx & 1;
+            // everything that does not depend on the accumulator is fetched before waiting for it:
+            // the tile's column norms (shared), this row's norm and its first old values
+            colnrm[tt] = n0 + tt < nn ? nrm[n0 + tt] : 0.0f;
+            const int k = m0 + r, k0 = m0 + wq * 32;
+            const bool krow = k < nn;  // rows past the network (last block's padding) hold nothing
+            const float nk_ = krow ? nrm[k] : 0.0f;
+            const float *xrow = X + (size_t)(krow ? k : 0) * ld + n0 + half * 128;
+            float nxt[16];
+            if (krow && n0 + half * 128 < ld)
+                ld16(xrow, nxt);
+            epi_bar2();
             // on a timed-out wait every epilogue warp still runs the named barriers below
             const bool live = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, ctl) &&
                               !*(volatile int *)&sy.abort;
             tc_fence_after();
-            const int k = m0 + r, k0 = m0 + wq * 32;
-            const bool krow = k < nn;  // rows past the network (last block's padding) hold nothing
-            const float nk_ = krow ? nrm[k] : 0.0f;
             float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
-            const float *xrow = X + (size_t)(krow ? k : 0) * ld + n0 + half * 128;
-            float nxt[16];
-            if (live && krow && n0 + half * 128 < ld)
-                ld16(xrow, nxt);
 #pragma unroll 1
             for (int c = 0; c < 8 && live; ++c) {  // eight 16-column sub-chunks of this warp's 128 columns
                 const int cc = half * 128 + c * 16, j0 = n0 + cc;
-                const size_t o = (size_t)k * ld + j0;
                 const bool inside = krow && j0 < ld;
                 float old[16], acc[16];
 #pragma unroll
@@ -698,7 +681,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                     old[q] = inside ? nxt[q] : 0.0f;
                 if (c < 7 && krow && j0 + 16 < ld)
                     ld16(xrow + (c + 1) * 16, nxt);  // next sub-chunk's old values, in flight meanwhile
-                const float nj = j0 + (lane & 15) < nn ? nrm[j0 + (lane & 15)] : 0.0f;
                 tmem_ld16(sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16) + cc, acc);
                 if (c == 7) {  // this warp is done with the accumulator: tell the even CTA
                     tc_fence_before();
@@ -716,7 +698,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                 }
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float s = tanimoto_fast(acc[q], nk_, __shfl_sync(0xffffffffu, nj, q));
+                    const float s = tanimoto_fast(acc[q], nk_, colnrm[cc + q]);
                     const bool valid = (vmask >> q) & 1u;
                     const float v = valid ? fmaf(a, s, keep * old[q]) : old[q];
                     const float x = valid ? (SIM_SIGMA ? s : v) : 0.0f;
@@ -727,57 +709,92 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                     old[q] = v;
                     acc[q] = x;
                 }
-                // stores: FP32 upper triangle, split copies in both orientations
-                uint32_t hv[8], lv[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    split_pair(old[2 * q], old[2 * q + 1], hv[q], lv[q]);
-                if (vmask == 0xffffu) {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        reinterpret_cast<float4 *>(X + o)[q] =
-                            make_float4(old[4 * q], old[4 * q + 1], old[4 * q + 2], old[4 * q + 3]);
-                } else if (vmask) {
-#pragma unroll
-                    for (int q = 0; q < 16; ++q)
-                        if (vmask >> q & 1u)
-                            X[o + q] = old[q];
-                }
-                if (vmask) {
-                    st16_packed(Xh + o, hv, vmask);
-                    st16_packed(Xl + o, lv, vmask);
-                }
-                // mirrored entries (j, k): lane l writes row j0 + (l & 15), columns k0 + 16 (l >> 4) + 0..15
-                const int jm = j0 + (lane & 15), km = k0 + 16 * (lane >> 4);
-                const uint32_t mmask =
-                    jm >= nn ? 0u : (km + 15 < jm ? 0xffffu : (km >= jm ? 0u : ((1u << (jm - km)) - 1u)));
-                const size_t mo = (size_t)jm * ld + km;
-                store_transposed16(xp, hv, mmask ? Xh + mo : nullptr, mmask);
-                store_transposed16(xp, lv, mmask ? Xl + mo : nullptr, mmask);
-                // column sums over this warp's 32 rows (x in acc; under D2 also v^2)
+                // column sums of s under D2 (from registers; v sums come from the staged block)
                 if (SIM_SIGMA) {
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
-                        old[q] = (vmask >> q & 1u) ? old[q] * old[q] : 0.0f;
-                    const float t2 = lane_transpose_sum16(old);
-                    if (lane < 16)
-                        colred[(wq * 3 + 2) * N2 + cc + lane] = t2;
+                        old[q] = acc[q] * acc[q];
+                    const float t1 = lane_transpose_sum16(old);
+                    const float t0 = lane_transpose_sum16(acc);
+                    if (lane < 16) {
+                        colred[(wq * NS + 1) * N2 + cc + lane] = t1;
+                        colred[(wq * NS + 0) * N2 + cc + lane] = t0;
+                    }
                 }
+                // stage the new values (0 where nothing is stored) in this warp's block
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    old[q] = acc[q] * acc[q];
-                const float t1 = lane_transpose_sum16(old);
-                const float t0 = lane_transpose_sum16(acc);
-                if (lane < 16) {
-                    colred[(wq * 3 + 1) * N2 + cc + lane] = t1;
-                    colred[(wq * 3 + 0) * N2 + cc + lane] = t0;
+                    blk[lane * 17 + q] = (vmask >> q & 1u) ? old[q] : 0.0f;
+                __syncwarp();
+                // (a) row-major copies, coalesced: lane l takes 4 columns of rows (l >> 2) + 8 i
+#pragma unroll
+                for (int i2 = 0; i2 < 4; ++i2) {
+                    const int rr = (lane >> 2) + 8 * i2, kk = k0 + rr, jj = j0 + 4 * (lane & 3);
+                    float f[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        f[q] = blk[rr * 17 + 4 * (lane & 3) + q];
+                    uint32_t h2[2], l2[2];
+                    split_pair(f[0], f[1], h2[0], l2[0]);
+                    split_pair(f[2], f[3], h2[1], l2[1]);
+                    const size_t ro = (size_t)kk * ld + jj;
+                    if (kk < jj && jj + 3 < nn) {
+                        *reinterpret_cast<float4 *>(X + ro) = make_float4(f[0], f[1], f[2], f[3]);
+                        *reinterpret_cast<uint2 *>(Xh + ro) = make_uint2(h2[0], h2[1]);
+                        *reinterpret_cast<uint2 *>(Xl + ro) = make_uint2(l2[0], l2[1]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            if (kk < jj + q && jj + q < nn) {
+                                X[ro + q] = f[q];
+                                reinterpret_cast<uint16_t *>(Xh)[ro + q] = (uint16_t)(h2[q >> 1] >> (16 * (q & 1)));
+                                reinterpret_cast<uint16_t *>(Xl)[ro + q] = (uint16_t)(l2[q >> 1] >> (16 * (q & 1)));
+                            }
+                    }
                 }
+                // (b) mirrored entries (j, k): lane l takes column (l & 15), rows 16 (l >> 4) + 0..15,
+                //     and the column sums over the warp's 32 rows
+                {
+                    const int col = lane & 15, h16 = 16 * (lane >> 4);
+                    float g[16];
+#pragma unroll
+                    for (int m = 0; m < 16; ++m)
+                        g[m] = blk[(h16 + m) * 17 + col];
+                    float c1 = 0.0f, c2 = 0.0f;
+#pragma unroll
+                    for (int m = 0; m < 16; ++m) {
+                        c1 += g[m];
+                        c2 += g[m] * g[m];
+                    }
+                    c1 += __shfl_xor_sync(0xffffffffu, c1, 16);
+                    c2 += __shfl_xor_sync(0xffffffffu, c2, 16);
+                    if (lane < 16) {
+                        if (SIM_SIGMA) {
+                            colred[(wq * NS + 2) * N2 + cc + lane] = c2;  // sum of v^2
+                        } else {
+                            colred[(wq * NS + 0) * N2 + cc + lane] = c1;
+                            colred[(wq * NS + 1) * N2 + cc + lane] = c2;
+                        }
+                    }
+                    uint32_t hv[8], lv[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        split_pair(g[2 * q], g[2 * q + 1], hv[q], lv[q]);
+                    const int jm = j0 + col, km = k0 + h16;
+                    const uint32_t mmask =
+                        jm >= nn ? 0u : (km + 15 < jm ? 0xffffu : (km >= jm ? 0u : ((1u << (jm - km)) - 1u)));
+                    if (mmask) {
+                        const size_t mo = (size_t)jm * ld + km;
+                        st16_packed(Xh + mo, hv, mmask);
+                        st16_packed(Xl + mo, lv, mmask);
+                    }
+                }
+                __syncwarp();  // the block is rewritten by the next sub-chunk
             }
-            if (!SIM_SIGMA)
-                rv = r2;  // x = v under rules D1 and D0
-            rowred[(half * 3 + 0) * 128 + r] = r1;
-            rowred[(half * 3 + 1) * 128 + r] = r2;
-            rowred[(half * 3 + 2) * 128 + r] = rv;
+            rowred[(half * NS + 0) * 128 + r] = r1;
+            rowred[(half * NS + 1) * 128 + r] = r2;
+            if (SIM_SIGMA)
+                rowred[(half * NS + 2) * 128 + r] = rv;
             epi_bar2();
             if (live) {
 #pragma unroll
@@ -786,13 +803,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                                                                             : (isP ? d.ps_vsq : d.cs_vsq);
                     const int wc = (!SIM_SIGMA && w == 2) ? 1 : w;  // sum of v^2 = sum of x^2 unless D2
                     // column role: tile column tt, summed over this CTA's 128 rows
-                    const float cs = ((colred[(0 * 3 + wc) * N2 + tt] + colred[(1 * 3 + wc) * N2 + tt]) +
-                                      colred[(2 * 3 + wc) * N2 + tt]) + colred[(3 * 3 + wc) * N2 + tt];
+                    const float cs = ((colred[(0 * NS + wc) * N2 + tt] + colred[(1 * NS + wc) * N2 + tt]) +
+                                      colred[(2 * NS + wc) * N2 + tt]) + colred[(3 * NS + wc) * N2 + tt];
                     if (n0 + tt < ld)
                         S[(size_t)(nbk + 2 * bm + (int)rank) * ld + n0 + tt] = cs;
                     // row role: tile row tt of this CTA, summed over the 256 columns
                     if (tt < 128 && m0 + tt < ld)
-                        S[(size_t)bn * ld + m0 + tt] = rowred[(0 * 3 + w) * 128 + tt] + rowred[(1 * 3 + w) * 128 + tt];
+                        S[(size_t)bn * ld + m0 + tt] =
+                            rowred[(0 * NS + wc) * 128 + tt] + rowred[(1 * NS + wc) * 128 + tt];
                 }
             }
             epi_bar2();
@@ -899,10 +917,10 @@ cudaError_t set_smem_limits()
     if ((e = cudaFuncSetAttribute(k_tc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phase1_smem())))
         return e;
     if ((e = cudaFuncSetAttribute(k_tc_phase2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)phase2_smem())))
+                                  (int)phase2_smem<false>())))
         return e;
     if ((e = cudaFuncSetAttribute(k_tc_phase2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)phase2_smem())))
+                                  (int)phase2_smem<true>())))
         return e;
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
     if ((e = cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem)))
@@ -997,9 +1015,9 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
         return e;
     ke.mark(s);
     if (d.diag == 2)
-        k_tc_phase2<true><<<h.grid2, THREADS2, phase2_smem(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
+        k_tc_phase2<true><<<h.grid2, THREADS2, phase2_smem<true>(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
     else
-        k_tc_phase2<false><<<h.grid2, THREADS2, phase2_smem(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
+        k_tc_phase2<false><<<h.grid2, THREADS2, phase2_smem<false>(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
     ke.mark(s);
     return launch_fin_tail(d, s, ke);
 }
