@@ -38,15 +38,12 @@ namespace {
 
 using namespace tc;
 
-constexpr int BN1 = 256;     // phase-1 tile width (genes)
-constexpr int ST1 = 2;       // phase-1 pipeline stages (96 KB each)
 
-struct TcMaps {
-    CUtensorMap Ph, Pl;              // P_off split   [Tp][Tp]  box 64 x 128
-    CUtensorMap Wh[2], Wl[2];        // W split       [Tp][Gp]  box 64 x 128
-    CUtensorMap Wth1[2], Wtl1[2];    // W^T split     [Gp][Tp]  box 64 x BN1
-    CUtensorMap Wth2[2], Wtl2[2];    // W^T split     [Gp][Tp]  box 64 x 128
-    CUtensorMap Ch1, Cl1;            // C_off split   [Gp][Gp]  box 64 x BN1
+struct TcMaps {  // split copies, K-major, boxes of 64 x 128 (one CTA's half of a 256-row tile)
+    CUtensorMap Ph, Pl;              // P_off split   [Tp][Tp]
+    CUtensorMap Wh[2], Wl[2];        // W split       [Tp][Gp]
+    CUtensorMap Wth[2], Wtl[2];      // W^T split     [Gp][Tp]
+    CUtensorMap Ch, Cl;              // C_off split   [Gp][Gp]
 };
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
@@ -78,6 +75,40 @@ __global__ void k_split(const float *__restrict__ X, size_t n, __nv_bfloat16 *__
         split_bf16(X[q], H[q], L[q]);
 }
 
+// hi / lo of two values at once, packed as BF16 pairs (first value in the low half)
+__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+__device__ __forceinline__ void ld16(const float *src, float (&v)[16])
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 x = reinterpret_cast<const float4 *>(src)[q];
+        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+}
+
+// 16 BF16 values held as 8 packed pairs: two 16-byte stores, or the masked entries
+__device__ __forceinline__ void st16_packed(__nv_bfloat16 *dst, const uint32_t (&p)[8], uint32_t mask)
+{
+    if (mask == 0xffffu) {
+        reinterpret_cast<uint4 *>(dst)[0] = make_uint4(p[0], p[1], p[2], p[3]);
+        reinterpret_cast<uint4 *>(dst)[1] = make_uint4(p[4], p[5], p[6], p[7]);
+    } else {
+        uint16_t *d16 = reinterpret_cast<uint16_t *>(dst);
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            if (mask >> q & 1u)
+                d16[q] = (uint16_t)(p[q >> 1] >> (16 * (q & 1)));
+    }
+}
+
 template <int STAGES>
 __device__ __forceinline__ void init_sync(Sync<STAGES> &sy)
 {
@@ -98,29 +129,6 @@ __device__ __forceinline__ void st32(float *dst, const float (&v)[32])
 #pragma unroll
     for (int q = 0; q < 8; ++q)
         reinterpret_cast<float4 *>(dst)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-}
-
-__device__ __forceinline__ void ld32(const float *src, float (&v)[32])
-{
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float4 x = reinterpret_cast<const float4 *>(src)[q];
-        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-    }
-}
-
-// 32 consecutive BF16 (64 bytes, 16-byte aligned destination)
-__device__ __forceinline__ void st32_bf16(__nv_bfloat16 *dst, const __nv_bfloat16 (&v)[32])
-{
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        uint4 u;
-        u.x = (uint32_t)__bfloat16_as_ushort(v[8 * q + 0]) | ((uint32_t)__bfloat16_as_ushort(v[8 * q + 1]) << 16);
-        u.y = (uint32_t)__bfloat16_as_ushort(v[8 * q + 2]) | ((uint32_t)__bfloat16_as_ushort(v[8 * q + 3]) << 16);
-        u.z = (uint32_t)__bfloat16_as_ushort(v[8 * q + 4]) | ((uint32_t)__bfloat16_as_ushort(v[8 * q + 5]) << 16);
-        u.w = (uint32_t)__bfloat16_as_ushort(v[8 * q + 6]) | ((uint32_t)__bfloat16_as_ushort(v[8 * q + 7]) << 16);
-        reinterpret_cast<uint4 *>(dst)[q] = u;
-    }
 }
 
 // ---------------------------------------------------------------------------
@@ -298,149 +306,258 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Phase 1 (grid: x = T tile of 128, y = G tile of BN1)
+// Phase 1 on CTA pairs: one 256 (TFs) x 256 (genes) tile of W' per pair
+// (grid x = 2 x T tiles, y = G tiles).  CTA r loads rows 128 r .. + 127 of
+// the tile's A blocks (P_off for R, W for A) and of its B blocks (W^T for R,
+// C_off for A); the even CTA issues cta_group::2 MMAs into two TMEM
+// accumulators of 256 columns (R at column 0, A at column 256).  Warps:
+// 0 TMA, 1 MMA (even CTA), 2-9 epilogue (two per TMEM lane quarter, each
+// taking 128 of the 256 columns in 16-column sub-chunks).
 // ---------------------------------------------------------------------------
+constexpr int ST1 = 3;
+constexpr uint32_t STAGE1 = 4 * A_BYTES;   // per CTA: A hi, A lo, B hi, B lo (128 rows each)
+constexpr int EPI1 = 8, THREADS1 = 64 + 32 * EPI1;
+
+struct Sync1 {
+    uint64_t full[ST1], empty[ST1];
+    uint64_t accum;
+    uint32_t tmem;
+    int abort, issued, consumed;
+};
+
+constexpr size_t P1_COLVEC = 3 * 256;   // c_j, |W_.j|^2, |C_.j|^2 of the tile's columns
+constexpr size_t P1_COLRED = 4 * 256;   // [quarter][column] sums of W'^2
+constexpr size_t P1_ROWRED = 2 * 128;   // [half][row] sums of W'^2
+constexpr size_t P1_BLK = 32 * 17;      // per epilogue warp: 32 x 16 staging block (padded)
+
 constexpr size_t phase1_smem()
 {
-    return 1024 + (size_t)ST1 * (2 * A_BYTES + 2 * BN1 * BK * 2) + sizeof(Sync<ST1>) + 16 +
-           4 * BN1 * sizeof(float) + 4 * sizeof(double);
+    return 1024 + (size_t)ST1 * STAGE1 + ((sizeof(Sync1) + 15) & ~size_t(15)) +
+           (P1_COLVEC + P1_COLRED + P1_ROWRED + EPI1 * P1_BLK) * sizeof(float) + EPI1 * sizeof(double);
 }
 
-__global__ void __launch_bounds__(THREADS, 1) k_tc_phase1(const __grid_constant__ TcMaps maps, Dev d, int cur)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
+    k_tc_phase1(const __grid_constant__ TcMaps maps, Dev d, int cur)
 {
     Ctl *ctl = d.ctl;
-    if (!ctl->active)
+    if (!ctl->active)  // both CTAs of a pair see the same value and leave together
         return;
-    constexpr int BN = BN1, STAGES = ST1;
-    constexpr uint32_t B_BYTES = BN * BK * 2, STAGE = 2 * A_BYTES + 2 * B_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
-    Sync<STAGES> &sy = *reinterpret_cast<Sync<STAGES> *>(stages + STAGES * STAGE);
-    float *colred = reinterpret_cast<float *>(stages + STAGES * STAGE + ((sizeof(Sync<STAGES>) + 15) & ~15));
-    double *hred = reinterpret_cast<double *>(colred + 4 * BN);
+    Sync1 &sy = *reinterpret_cast<Sync1 *>(stages + ST1 * STAGE1);
+    float *colvec = reinterpret_cast<float *>(stages + ST1 * STAGE1 + ((sizeof(Sync1) + 15) & ~size_t(15)));
+    float *colred = colvec + P1_COLVEC;
+    float *rowred = colred + P1_COLRED;
+    float *blocks = rowred + P1_ROWRED;
+    double *hred = reinterpret_cast<double *>(blocks + EPI1 * P1_BLK);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const uint32_t rank = cluster_ctarank();
+    const int mt = blockIdx.x >> 1, nt = blockIdx.y;
+    const int m0 = mt * 256 + 128 * (int)rank;  // this CTA's 128 rows (TFs)
+    const int n0 = nt * 256;                    // the tile's 256 columns (genes)
     const int nR = d.Tp / BK, nk = nR + d.Gp / BK;
 
-    if (threadIdx.x == 0)
-        init_sync(sy);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < ST1; ++q) {
+            mbar_init(&sy.full[q], 1);
+            mbar_init(&sy.empty[q], 1);
+        }
+        mbar_init(&sy.accum, 1);
+        sy.abort = 0;
+        sy.issued = 0;
+        sy.consumed = 0;
+        fence_mbar_init();
+    }
     if (warp == 1)
-        tmem_alloc(&sy.tmem, 2 * BN);
+        tmem_alloc_pair(&sy.tmem, 512);
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();
     tc_fence_after();
 
     if (warp == 0) {
-        if (lane == 0)
-            run_producer<STAGES>(sy, stages, STAGE, nk, ctl, [&](int kb, uint8_t *st, uint64_t *bar) {
+        if (lane == 0) {  // ---- TMA producer (both CTAs; completion counted on the even CTA) ----
+            const int nb0 = n0 + 128 * (int)rank;  // this CTA's half of the B rows
+            int kb = 0;
+            for (; kb < nk; ++kb) {
+                const int st = kb % ST1;
+                if (!wait_bounded(&sy.empty[st], ((uint32_t)(kb / ST1) & 1u) ^ 1u, &sy.abort, ctl))
+                    break;
+                const uint32_t fb = mapa_shared(smem_u32(&sy.full[st]), 0);
+                if (rank == 0)
+                    mbar_arrive_expect_tx(&sy.full[st], 2 * STAGE1);
+                uint8_t *b = stages + (size_t)st * STAGE1;
                 if (kb < nR) {  // responsibility: P_off rows x W^T rows, K over TFs
                     const int k = kb * BK;
-                    tma_load_2d(st, &maps.Ph, bar, k, m0);
-                    tma_load_2d(st + A_BYTES, &maps.Pl, bar, k, m0);
-                    tma_load_2d(st + 2 * A_BYTES, &maps.Wth1[cur], bar, k, n0);
-                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.Wtl1[cur], bar, k, n0);
+                    tma_load_2d_pair(b, &maps.Ph, fb, k, m0);
+                    tma_load_2d_pair(b + A_BYTES, &maps.Pl, fb, k, m0);
+                    tma_load_2d_pair(b + 2 * A_BYTES, &maps.Wth[cur], fb, k, nb0);
+                    tma_load_2d_pair(b + 3 * A_BYTES, &maps.Wtl[cur], fb, k, nb0);
                 } else {        // availability: W rows x C_off rows, K over genes
                     const int k = (kb - nR) * BK;
-                    tma_load_2d(st, &maps.Wh[cur], bar, k, m0);
-                    tma_load_2d(st + A_BYTES, &maps.Wl[cur], bar, k, m0);
-                    tma_load_2d(st + 2 * A_BYTES, &maps.Ch1, bar, k, n0);
-                    tma_load_2d(st + 2 * A_BYTES + B_BYTES, &maps.Cl1, bar, k, n0);
+                    tma_load_2d_pair(b, &maps.Wh[cur], fb, k, m0);
+                    tma_load_2d_pair(b + A_BYTES, &maps.Wl[cur], fb, k, m0);
+                    tma_load_2d_pair(b + 2 * A_BYTES, &maps.Ch, fb, k, nb0);
+                    tma_load_2d_pair(b + 3 * A_BYTES, &maps.Cl, fb, k, nb0);
                 }
-            });
+            }
+            sy.issued = kb;
+        }
     } else if (warp == 1) {
-        if (lane == 0)
-            run_mma<STAGES, BN>(
-                sy, stages, STAGE, nk, ctl, [&](int kb) { return kb < nR ? 0u : (uint32_t)BN; },
-                [&](int kb) { return kb == 0 || kb == nR; });
-    } else {
-        // ---- epilogue: one row of the tile per thread ----
-        const int wq = warp & 3, ew = warp - 2;
-        const int i = m0 + wq * 32 + lane;
-        const bool ok = wait_bounded(&sy.accum, 0, &sy.abort, ctl);
+        if (lane == 0 && rank == 0) {  // ---- MMA issuer of the pair ----
+            constexpr uint32_t idesc = idesc_bf16_f32(256, 256);
+            int kb = 0;
+            for (; kb < nk; ++kb) {
+                const int st = kb % ST1;
+                if (!wait_bounded(&sy.full[st], (uint32_t)(kb / ST1) & 1u, &sy.abort, ctl))
+                    break;
+                tc_fence_after();
+                const uint32_t base = smem_u32(stages + (size_t)st * STAGE1);
+                const uint32_t dacc = sy.tmem + (kb < nR ? 0u : 256u);
+                const bool fresh = kb == 0 || kb == nR;
+#pragma unroll
+                for (int kk = 0; kk < BK / 16; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint64_t ah = sdesc_k_sw128(base + off);
+                    const uint64_t al = sdesc_k_sw128(base + A_BYTES + off);
+                    const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
+                    const uint64_t bl = sdesc_k_sw128(base + 3 * A_BYTES + off);
+                    mma_bf16_pair(dacc, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
+                    mma_bf16_pair(dacc, ah, bl, idesc, 1u);
+                    mma_bf16_pair(dacc, al, bh, idesc, 1u);
+                }
+                mma_commit_pair(&sy.empty[st]);
+            }
+            sy.consumed = kb;
+            mma_commit_pair(&sy.accum);  // also on abort, so the epilogues can drain
+        }
+    } else {  // ---- epilogue: warps 2..9 of both CTAs ----
+        const int e = warp - 2, wq = warp & 3, half = e >> 2;
+        const int r = wq * 32 + lane, i = m0 + r, k0 = m0 + wq * 32;
+        const int tt = threadIdx.x - 64;  // 0..255
+        float *blk = blocks + (size_t)e * P1_BLK;
+        const int nx = cur ^ 1;
+        const float *W = d.W[cur];
+        float *Wn = d.W[nx];
+        __nv_bfloat16 *Wh = d.Wh[nx], *Wl = d.Wl[nx], *Wth = d.Wth[nx], *Wtl = d.Wtl[nx];
+        // what does not depend on the accumulators is fetched before waiting for them
+        {
+            const int j = n0 + tt;
+            const bool cj = j < d.G;
+            colvec[tt] = cj ? d.cdf[j] : 0.0f;
+            colvec[256 + tt] = cj ? d.csqW[j] : 0.0f;
+            colvec[512 + tt] = cj ? d.csqC[j] : 0.0f;
+        }
+        const bool ri = i < d.T;
+        const float pdi = ri ? d.pdf[i] : 0.0f, rsp = ri ? d.rsqP[i] : 0.0f, rsw = ri ? d.rsqW[i] : 0.0f;
+        const float *wrow = W + (size_t)i * d.Gp + n0 + half * 128;
+        float nxt[16];
+        ld16(wrow, nxt);
+        epi_bar2();
+        const bool live = wait_bounded(&sy.accum, 0, &sy.abort, ctl) && !*(volatile int *)&sy.abort;
         tc_fence_after();
-        const bool live = ok && !*(volatile int *)&sy.abort;
+        const float a = ctl->alpha, keep = 1.0f - a, halfa = 0.5f * a;
         float rowsq = 0.0f, hsum = 0.0f;
-        if (live) {
-            const bool ri = i < d.T;
-            const float pdi = ri ? d.pdf[i] : 0.0f, rsp = ri ? d.rsqP[i] : 0.0f, rsw = ri ? d.rsqW[i] : 0.0f;
-            const float a = ctl->alpha, keep = 1.0f - a, half = 0.5f * a;
-            const int nx = cur ^ 1;
-            const float *W = d.W[cur];
-            float *Wn = d.W[nx];
-            __nv_bfloat16 *Wh = d.Wh[nx], *Wl = d.Wl[nx], *Wth = d.Wth[nx], *Wtl = d.Wtl[nx];
-            const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
+        const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                const int j0 = n0 + c * 32;
-                if (j0 >= d.Gp) {  // beyond the padded width (warp-uniform)
-                    colred[ew * BN + c * 32 + lane] = 0.0f;
-                    continue;
-                }
-                float rr[32], aa[32], w[32], wn[32];
-                tmem_ld32(trow + c * 32, rr);
-                tmem_ld32(trow + BN + c * 32, aa);
-                const size_t o = (size_t)i * d.Gp + j0;
-                ld32(W + o, w);
-                __nv_bfloat16 hv[32], lv[32];
+        for (int c = 0; c < 8 && live; ++c) {
+            const int cc = half * 128 + c * 16, j0 = n0 + cc;
+            float w[16], rr[16], aa[16], wn[16];
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int j = j0 + q;
-                    wn[q] = 0.0f;
-                    if (ri && j < d.G) {
-                        const float rnum = rr[q] + pdi * w[q];       // P_i. . W_.j
-                        const float anum = aa[q] + w[q] * d.cdf[j];  // W_i. . C_.j
-                        const float R = tanimoto_fast(rnum, rsp, d.csqW[j]);
-                        const float A = tanimoto_fast(anum, rsw, d.csqC[j]);
-                        wn[q] = keep * w[q] + half * (A + R);
-                        hsum += fabsf(wn[q] - w[q]);
-                        rowsq += wn[q] * wn[q];
-                    }
-                    split_bf16(wn[q], hv[q], lv[q]);
-                }
-                st32(Wn + o, wn);
-                st32_bf16(Wh + o, hv);
-                st32_bf16(Wl + o, lv);
+            for (int q = 0; q < 16; ++q)
+                w[q] = nxt[q];
+            if (c < 7)
+                ld16(wrow + (c + 1) * 16, nxt);  // next sub-chunk's W, in flight meanwhile
+            tmem_ld16(trow + cc, rr);
+            tmem_ld16(trow + 256 + cc, aa);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {  // transposed copies: lanes write consecutive TFs
-                    Wth[(size_t)(j0 + q) * d.Tp + i] = hv[q];
-                    Wtl[(size_t)(j0 + q) * d.Tp + i] = lv[q];
+            for (int q = 0; q < 16; ++q) {
+                wn[q] = 0.0f;
+                if (ri && j0 + q < d.G) {
+                    const float rnum = rr[q] + pdi * w[q];               // P_i. . W_.j
+                    const float anum = aa[q] + w[q] * colvec[cc + q];    // W_i. . C_.j
+                    const float R = tanimoto_fast(rnum, rsp, colvec[256 + cc + q]);
+                    const float A = tanimoto_fast(anum, rsw, colvec[512 + cc + q]);
+                    wn[q] = keep * w[q] + halfa * (A + R);
+                    hsum += fabsf(wn[q] - w[q]);
+                    rowsq += wn[q] * wn[q];
                 }
-#pragma unroll
-                for (int q = 0; q < 32; ++q)
-                    wn[q] *= wn[q];
-                colred[ew * BN + c * 32 + lane] = lane_transpose_sum(wn);
+                blk[lane * 17 + q] = wn[q];
             }
-        }
-        epi_bar();
-        const int t = threadIdx.x - 64;  // 0..127
-        if (live) {
-            for (int col = t; col < BN; col += 128) {
-                const int j = n0 + col;
-                if (j < d.Gp)
-                    d.wcol_part[(size_t)blockIdx.x * d.Gp + j] =
-                        ((colred[col] + colred[BN + col]) + colred[2 * BN + col]) + colred[3 * BN + col];
+            __syncwarp();
+            // (a) W' and its split copies, row-major and coalesced: lane l takes 4 columns of rows (l >> 2) + 8 i
+#pragma unroll
+            for (int i2 = 0; i2 < 4; ++i2) {
+                const int rr2 = (lane >> 2) + 8 * i2, jj = j0 + 4 * (lane & 3);
+                float f[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    f[q] = blk[rr2 * 17 + 4 * (lane & 3) + q];
+                uint32_t h2[2], l2[2];
+                split_pair(f[0], f[1], h2[0], l2[0]);
+                split_pair(f[2], f[3], h2[1], l2[1]);
+                const size_t ro = (size_t)(k0 + rr2) * d.Gp + jj;
+                *reinterpret_cast<float4 *>(Wn + ro) = make_float4(f[0], f[1], f[2], f[3]);
+                *reinterpret_cast<uint2 *>(Wh + ro) = make_uint2(h2[0], h2[1]);
+                *reinterpret_cast<uint2 *>(Wl + ro) = make_uint2(l2[0], l2[1]);
             }
-            d.wrow_part[(size_t)blockIdx.y * d.Tp + i] = rowsq;
+            // (b) the transposed split copies: lane l takes column (l & 15), rows 16 (l >> 4) + 0..15,
+            //     and the column sums of W'^2 over the warp's 32 rows
+            {
+                const int col = lane & 15, h16 = 16 * (lane >> 4);
+                float g[16];
+#pragma unroll
+                for (int m = 0; m < 16; ++m)
+                    g[m] = blk[(h16 + m) * 17 + col];
+                float c2 = 0.0f;
+#pragma unroll
+                for (int m = 0; m < 16; ++m)
+                    c2 += g[m] * g[m];
+                c2 += __shfl_xor_sync(0xffffffffu, c2, 16);
+                if (lane < 16)
+                    colred[wq * 256 + cc + lane] = c2;
+                uint32_t hv[8], lv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q)
+                    split_pair(g[2 * q], g[2 * q + 1], hv[q], lv[q]);
+                const size_t to = (size_t)(j0 + col) * d.Tp + k0 + h16;
+                st16_packed(Wth + to, hv, 0xffffu);
+                st16_packed(Wtl + to, lv, 0xffffu);
+            }
+            __syncwarp();
         }
+        rowred[half * 128 + r] = rowsq;
         double hv = (double)hsum;
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1)
             hv += __shfl_xor_sync(0xffffffffu, hv, off);
         if (lane == 0)
-            hred[ew] = hv;
-        epi_bar();
-        if (t == 0 && live)
-            d.hpart[(size_t)blockIdx.y * d.nbT + blockIdx.x] = ((hred[0] + hred[1]) + hred[2]) + hred[3];
+            hred[e] = hv;
+        epi_bar2();
+        if (live) {
+            const int slot = m0 / 128;  // this CTA's 128-row block
+            if (n0 + tt < d.Gp)
+                d.wcol_part[(size_t)slot * d.Gp + n0 + tt] =
+                    ((colred[tt] + colred[256 + tt]) + colred[512 + tt]) + colred[768 + tt];
+            if (tt < 128)
+                d.wrow_part[(size_t)nt * d.Tp + m0 + tt] = rowred[tt] + rowred[128 + tt];
+            if (tt == 0) {
+                double hs = 0.0;
+                for (int q = 0; q < EPI1; ++q)
+                    hs += hred[q];
+                d.hpart[(size_t)nt * d.nbT + slot] = hs;
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0)
-        drain(sy, ctl);
-    __syncthreads();
+    if (threadIdx.x == 0 && rank == 0)  // loads counted here but not consumed (abort only)
+        for (int kb = sy.consumed; kb < sy.consumed + ST1 && kb < sy.issued; ++kb)
+            wait_bounded(&sy.full[kb % ST1], (uint32_t)(kb / ST1) & 1u, &sy.abort, ctl, true);
+    cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        tmem_dealloc(sy.tmem, 2 * BN);
+        tmem_dealloc_pair(sy.tmem, 512);
     }
 }
 
@@ -490,40 +607,6 @@ constexpr size_t phase2_smem()
     using C = P2Cfg<SIM>;
     return 1024 + (size_t)C::ST * STAGE2 + ((sizeof(Sync2T<C::ST>) + 15) & ~size_t(15)) +
            (C::COLRED + C::ROWRED + C::COLNRM + EPI2 * C::BLK) * sizeof(float);
-}
-
-// hi / lo of two values at once, packed as BF16 pairs (first value in the low half)
-__device__ __forceinline__ void split_pair(float x0, float x1, uint32_t &hi, uint32_t &lo)
-{
-    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
-    const float2 hf = __bfloat1622float2(h);
-    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
-    hi = *reinterpret_cast<const uint32_t *>(&h);
-    lo = *reinterpret_cast<const uint32_t *>(&l);
-}
-
-__device__ __forceinline__ void ld16(const float *src, float (&v)[16])
-{
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float4 x = reinterpret_cast<const float4 *>(src)[q];
-        v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
-    }
-}
-
-// 16 BF16 values held as 8 packed pairs: two 16-byte stores, or the masked entries
-__device__ __forceinline__ void st16_packed(__nv_bfloat16 *dst, const uint32_t (&p)[8], uint32_t mask)
-{
-    if (mask == 0xffffu) {
-        reinterpret_cast<uint4 *>(dst)[0] = make_uint4(p[0], p[1], p[2], p[3]);
-        reinterpret_cast<uint4 *>(dst)[1] = make_uint4(p[4], p[5], p[6], p[7]);
-    } else {
-        uint16_t *d16 = reinterpret_cast<uint16_t *>(dst);
-#pragma unroll
-        for (int q = 0; q < 16; ++q)
-            if (mask >> q & 1u)
-                d16[q] = (uint16_t)(p[q >> 1] >> (16 * (q & 1)));
-    }
 }
 
 template <bool SIM_SIGMA>
@@ -579,8 +662,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                 const bool isP = tile < 0;
                 const int m0 = ((tile >> 16) & 0x7fff) * N2 + 128 * rank, n0 = (tile & 0xffff) * N2 + 128 * rank;
                 const int nk = (isP ? d.Gp : d.Tp) / BK;
-                const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Wth2[cur];
-                const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl2[cur];
+                const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Wth[cur];
+                const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl[cur];
                 for (int kb = 0; kb < nk; ++kb, ++g) {
                     const int st = g % ST2;
                     if (!wait_bounded(&sy.empty[st], ((uint32_t)(g / ST2) & 1u) ^ 1u, &sy.abort, ctl)) {
@@ -966,15 +1049,13 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s)
         std::memset(m, 0, sizeof *m);
         d.tc_host = h;
         if ((e = make_map(&m->Ph, d.Ph, d.Tp, d.Tp, 128)) || (e = make_map(&m->Pl, d.Pl, d.Tp, d.Tp, 128)) ||
-            (e = make_map(&m->Ch1, d.Ch, d.Gp, d.Gp, BN1)) || (e = make_map(&m->Cl1, d.Cl, d.Gp, d.Gp, BN1)))
+            (e = make_map(&m->Ch, d.Ch, d.Gp, d.Gp, 128)) || (e = make_map(&m->Cl, d.Cl, d.Gp, d.Gp, 128)))
             return e;
         for (int b = 0; b < 2; ++b)
             if ((e = make_map(&m->Wh[b], d.Wh[b], d.Tp, d.Gp, 128)) ||
                 (e = make_map(&m->Wl[b], d.Wl[b], d.Tp, d.Gp, 128)) ||
-                (e = make_map(&m->Wth1[b], d.Wth[b], d.Gp, d.Tp, BN1)) ||
-                (e = make_map(&m->Wtl1[b], d.Wtl[b], d.Gp, d.Tp, BN1)) ||
-                (e = make_map(&m->Wth2[b], d.Wth[b], d.Gp, d.Tp, 128)) ||
-                (e = make_map(&m->Wtl2[b], d.Wtl[b], d.Gp, d.Tp, 128)))
+                (e = make_map(&m->Wth[b], d.Wth[b], d.Gp, d.Tp, 128)) ||
+                (e = make_map(&m->Wtl[b], d.Wtl[b], d.Gp, d.Tp, 128)))
                 return e;
         int dev = 0, nsm = 0;
         if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
@@ -1007,8 +1088,8 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
     const TcHost &h = *static_cast<const TcHost *>(d.tc_host);
     const TcMaps &m = h.maps;
     ke.mark(s);
-    dim3 g1(d.nbT, ceil_div(d.Gp, BN1));
-    k_tc_phase1<<<g1, THREADS, phase1_smem(), s>>>(m, d, cur);
+    dim3 g1(2 * (d.Tp / 256), d.Gp / 256);
+    k_tc_phase1<<<g1, THREADS1, phase1_smem(), s>>>(m, d, cur);
     ke.mark(s);
     cudaError_t e = launch_reduce_wnorms(d, s);
     if (e)

@@ -461,7 +461,9 @@ int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P
 
     panda_ctx *c = new panda_ctx();
     c->T = T; c->G = G;
-    c->Tp = round_up(T, TILE); c->Gp = round_up(G, TILE);
+    // the tensor-core path works on 256-row tiles of CTA pairs: pad to 256 there
+    const int granule = opts.prec == PANDA_BF16X3 ? 2 * TILE : TILE;
+    c->Tp = round_up(T, granule); c->Gp = round_up(G, granule);
     c->nbT = c->Tp / TILE; c->nbG = c->Gp / TILE;
     c->prec = opts.prec; c->diag = opts.diag; c->normalize = opts.normalize;
     c->graph_iters = (opts.graph_iters + 1) & ~1;  // even: a graph returns to its start buffer
