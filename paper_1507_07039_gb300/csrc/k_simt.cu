@@ -212,24 +212,54 @@ __global__ void __launch_bounds__(NT, 2) k_phase1(Dev d, int cur)
         d.hpart[(size_t)blockIdx.y * d.nbT + blockIdx.x] = hred[0];
 }
 
-// rsqW[i] = sum_b wrow_part[b][i], csqW[j] = sum_b wcol_part[b][j] (FP64, b in order)
-__global__ void k_reduce_wnorms(Dev d)
+// Slot sums for 32 consecutive rows per block, 8 threads per row: thread
+// (g, x) adds slots g, g + 8, g + 16, ... of row x in FP64, then the 8 partial
+// sums are added in group order (a fixed order, so the result is deterministic).
+constexpr int RS_ROWS = 32, RS_GROUPS = 8;
+
+template <int NV>
+__device__ __forceinline__ void slot_sums(const float *const (&src)[NV], int nslot, int ld, int x, bool ok,
+                                          double (&out)[NV], double (*sh)[RS_GROUPS][RS_ROWS])
+{
+    const int lx = threadIdx.x & (RS_ROWS - 1), g = threadIdx.x / RS_ROWS;
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        acc[v] = 0.0;
+    if (ok)
+        for (int b = g; b < nslot; b += RS_GROUPS)
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                acc[v] += (double)src[v][(size_t)b * ld + x];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+        sh[v][g][lx] = acc[v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double t = 0.0;
+        for (int q = 0; q < RS_GROUPS; ++q)
+            t += sh[v][q][lx];
+        out[v] = t;
+    }
+}
+
+// rsqW[i] = sum_b wrow_part[b][i], csqW[j] = sum_b wcol_part[b][j] (FP64).
+// Blocks [0, ceil(T/32)) take rows of W, the rest its columns.
+__global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_reduce_wnorms(Dev d)
 {
     if (!d.ctl->active)
         return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < d.T) {
-        double s = 0.0;
-        for (int b = 0; b < d.nbG; ++b)
-            s += (double)d.wrow_part[(size_t)b * d.Tp + x];
-        d.rsqW[x] = (float)s;
-    } else if (x - d.T < d.G) {
-        const int j = x - d.T;
-        double s = 0.0;
-        for (int b = 0; b < d.nbT; ++b)
-            s += (double)d.wcol_part[(size_t)b * d.Gp + j];
-        d.csqW[j] = (float)s;
-    }
+    __shared__ double sh[1][RS_GROUPS][RS_ROWS];
+    const int bT = ceil_div(d.T, RS_ROWS);
+    const bool rows = (int)blockIdx.x < bT;
+    const int x = ((rows ? blockIdx.x : blockIdx.x - bT) * RS_ROWS) + (threadIdx.x & (RS_ROWS - 1));
+    const bool ok = x < (rows ? d.T : d.G);
+    const float *const src[1] = {rows ? d.wrow_part : d.wcol_part};
+    double out[1];
+    slot_sums<1>(src, rows ? d.nbG : d.nbT, rows ? d.Tp : d.Gp, x, ok, out, sh);
+    if (ok && threadIdx.x < RS_ROWS)
+        (rows ? d.rsqW : d.csqW)[x] = (float)out[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -357,30 +387,29 @@ __global__ void __launch_bounds__(NT, 2) k_phase2(Dev d, int cur)
 }
 
 // ---------------------------------------------------------------------------
-// Eq. 6 diagonals and the squared norms of P' and C' (one thread per row)
+// Eq. 6 diagonals and the squared norms of P' and C' (32 rows per block, the
+// row partial sums added by 8 threads per row).  Blocks [0, ceil(T/32)) take
+// rows of P, the rest rows of C.
 // ---------------------------------------------------------------------------
-__global__ void k_fin(Dev d)
+__global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_fin(Dev d)
 {
     const Ctl *ctl = d.ctl;
     if (!ctl->active)
         return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool isP = x < d.T;
-    if (!isP && x - d.T >= d.G)
-        return;
-    const int i = isP ? x : x - d.T;
+    __shared__ double sh[3][RS_GROUPS][RS_ROWS];
+    const int bT = ceil_div(d.T, RS_ROWS);
+    const bool isP = (int)blockIdx.x < bT;
+    const int i = ((isP ? blockIdx.x : blockIdx.x - bT) * RS_ROWS) + (threadIdx.x & (RS_ROWS - 1));
     const int n = isP ? d.T : d.G;       // network size
+    const bool ok = i < n;
     const int nb = isP ? (d.nsP ? d.nsP : d.nbT) : (d.nsC ? d.nsC : d.nbG);  // partial-sum slots
     const int ld = isP ? d.Tp : d.Gp;
-    const float *S1 = isP ? d.ps_sum : d.cs_sum;
-    const float *S2 = isP ? d.ps_sq : d.cs_sq;
-    const float *SV = isP ? d.ps_vsq : d.cs_vsq;
-    double s1 = 0.0, s2 = 0.0, sv = 0.0;
-    for (int b = 0; b < nb; ++b) {
-        s1 += (double)S1[(size_t)b * ld + i];
-        s2 += (double)S2[(size_t)b * ld + i];
-        sv += (double)SV[(size_t)b * ld + i];
-    }
+    const float *const src[3] = {isP ? d.ps_sum : d.cs_sum, isP ? d.ps_sq : d.cs_sq, isP ? d.ps_vsq : d.cs_vsq};
+    double sums[3];
+    slot_sums<3>(src, nb, ld, i, ok, sums, sh);
+    if (!ok || threadIdx.x >= RS_ROWS)
+        return;
+    const double s1 = sums[0], s2 = sums[1], sv = sums[2];
     const double alpha = (double)ctl->alpha;
     const int t = ctl->iters + 1;
     const double growth = d.e2tab[t < HIST_CAP ? t : HIST_CAP];
@@ -443,13 +472,13 @@ const char *const SIMT_KERNEL_NAMES[SIMT_KERNELS] = {"k_rn", "k_phase1", "k_redu
 
 cudaError_t launch_reduce_wnorms(const Dev &d, cudaStream_t s)
 {
-    k_reduce_wnorms<<<ceil_div(d.T + d.G, 256), 256, 0, s>>>(d);
+    k_reduce_wnorms<<<ceil_div(d.T, RS_ROWS) + ceil_div(d.G, RS_ROWS), RS_ROWS * RS_GROUPS, 0, s>>>(d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fin_tail(const Dev &d, cudaStream_t s, KernelEvents &ke)
 {
-    k_fin<<<ceil_div(d.T + d.G, 256), 256, 0, s>>>(d);
+    k_fin<<<ceil_div(d.T, RS_ROWS) + ceil_div(d.G, RS_ROWS), RS_ROWS * RS_GROUPS, 0, s>>>(d);
     ke.mark(s);
     k_tail<<<1, 256, 0, s>>>(d);
     ke.mark(s);
@@ -464,7 +493,7 @@ cudaError_t launch_iteration_simt(const Dev &d, int cur, cudaStream_t s, KernelE
     ke.mark(s);
     k_phase1<<<g1, NT, 0, s>>>(d, cur);
     ke.mark(s);
-    k_reduce_wnorms<<<ceil_div(d.T + d.G, 256), 256, 0, s>>>(d);
+    launch_reduce_wnorms(d, s);
     ke.mark(s);
     const int tiles = d.nbT * (d.nbT + 1) / 2 + d.nbG * (d.nbG + 1) / 2;
     if (d.diag == 2)
