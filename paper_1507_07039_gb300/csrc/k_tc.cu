@@ -754,22 +754,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                               !*(volatile int *)&sy.abort;
             tc_fence_after();
             float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
+            const uint32_t tbase = sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16) + half * 128;
+            uint32_t accn[16];
+            if (live) {
+                tmem_ld16_nowait(tbase, accn);
+                tmem_wait();
+            }
 #pragma unroll 1
             for (int c = 0; c < 8 && live; ++c) {  // eight 16-column sub-chunks of this warp's 128 columns
                 const int cc = half * 128 + c * 16, j0 = n0 + cc;
                 const bool inside = krow && j0 < ld;
                 float old[16], acc[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
+                for (int q = 0; q < 16; ++q) {
                     old[q] = inside ? nxt[q] : 0.0f;
-                if (c < 7 && krow && j0 + 16 < ld)
-                    ld16(xrow + (c + 1) * 16, nxt);  // next sub-chunk's old values, in flight meanwhile
-                tmem_ld16(sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16) + cc, acc);
-                if (c == 7) {  // this warp is done with the accumulator: tell the even CTA
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0)
-                        mbar_arrive_cluster(tempty_even + buf * (uint32_t)sizeof(uint64_t));
+                    acc[q] = __uint_as_float(accn[q]);
+                }
+                if (c < 7) {
+                    if (krow && j0 + 16 < ld)
+                        ld16(xrow + (c + 1) * 16, nxt);      // next sub-chunk's old values and
+                    tmem_ld16_nowait(tbase + (c + 1) * 16, accn);  // accumulator, in flight meanwhile
                 }
                 // interior sub-chunks of off-diagonal tiles are entirely valid
                 uint32_t vmask = 0xffffu;
@@ -779,9 +783,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                     for (int q = 0; q < 16; ++q)
                         vmask |= (k < j0 + q && j0 + q < nn) ? (1u << q) : 0u;
                 }
+                float nj[16];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 v4 = reinterpret_cast<const float4 *>(colnrm + cc)[q];
+                    nj[4 * q] = v4.x; nj[4 * q + 1] = v4.y; nj[4 * q + 2] = v4.z; nj[4 * q + 3] = v4.w;
+                }
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
-                    const float s = tanimoto_fast(acc[q], nk_, colnrm[cc + q]);
+                    const float s = tanimoto_fast(acc[q], nk_, nj[q]);
                     const bool valid = (vmask >> q) & 1u;
                     const float v = valid ? fmaf(a, s, keep * old[q]) : old[q];
                     const float x = valid ? (SIM_SIGMA ? s : v) : 0.0f;
@@ -873,6 +883,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                     }
                 }
                 __syncwarp();  // the block is rewritten by the next sub-chunk
+                tmem_wait();   // the next sub-chunk's accumulator has landed
+                if (c == 6) {  // that was the last load from this accumulator: tell the even CTA
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive_cluster(tempty_even + buf * (uint32_t)sizeof(uint64_t));
+                }
             }
             rowred[(half * NS + 0) * 128 + r] = r1;
             rowred[(half * NS + 1) * 128 + r] = r2;
