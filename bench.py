@@ -449,7 +449,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--cpu-frac", type=float, default=0.1)
-    ap.add_argument("--ref-frac", type=float, default=0.005)
+    ap.add_argument("--ref-frac", type=float, default=0.02)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
