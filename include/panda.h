@@ -169,6 +169,14 @@ int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, do
  * sm_103. */
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms);
 
+/* Test of the bounded device waits (no paper counterpart): runs the
+ * tensor-core self-test product with one pipeline stage armed but never
+ * loaded, so its barrier never completes; the kernel's bounded waits give up
+ * after about a second, drain, release TMEM and exit.  Returns
+ * PANDA_ETIMEOUT when that happened as intended (the device stays usable),
+ * 0 if the wait unexpectedly completed, another error otherwise. */
+int panda_selftest_timeout(void);
+
 /* The context's stream as a cudaStream_t. */
 void *panda_stream(const panda_ctx *ctx);
 

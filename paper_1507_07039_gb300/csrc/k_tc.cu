@@ -138,8 +138,11 @@ struct GemmMaps {
     CUtensorMap Ah, Al, Bh, Bl;
 };
 
+// stall_kb >= 0: the producer arms stage stall_kb but issues none of its loads,
+// so that stage's barrier never completes and the bounded waits must end the
+// kernel with ST_TIMEOUT (the timeout path's test).
 __global__ void __launch_bounds__(THREADS, 1)
-    k_tc_selftest(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl)
+    k_tc_selftest(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl, int stall_kb)
 {
     constexpr int BN = 128, STAGES = 3;
     constexpr uint32_t B_BYTES = BN * BK * 2, STAGE = 2 * A_BYTES + 2 * B_BYTES;
@@ -158,6 +161,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 0) {
         if (lane == 0)
             run_producer<STAGES>(sy, stages, STAGE, nk, ctl, [&](int kb, uint8_t *st, uint64_t *bar) {
+                if (kb == stall_kb)
+                    return;
                 tma_load_2d(st, &maps.Ah, bar, kb * BK, m0);
                 tma_load_2d(st + A_BYTES, &maps.Al, bar, kb * BK, m0);
                 tma_load_2d(st + 2 * A_BYTES, &maps.Bh, bar, kb * BK, n0);
@@ -167,8 +172,10 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0)
             run_mma<STAGES, BN>(sy, stages, STAGE, nk, ctl, [](int) { return 0u; }, [](int kb) { return kb == 0; });
     } else {
+        // the issuer commits `accum` on every path (abort included), so this wait
+        // also makes sure that arrival has landed before the CTA leaves
         const int wq = warp & 3;
-        const bool ok = wait_bounded(&sy.accum, 0, &sy.abort, ctl);
+        const bool ok = wait_bounded(&sy.accum, 0, &sy.abort, ctl, true);
         tc_fence_after();
         if (ok && !*(volatile int *)&sy.abort) {
             const int r = m0 + wq * 32 + lane;
@@ -1122,7 +1129,7 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
 
 // D = A . B^T on the tensor-core pipeline (self-test support)
 cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms,
-                             int pair, int *status)
+                             int pair, int stall_kb, int *status)
 {
     cudaError_t e = set_smem_limits();
     if (e)
@@ -1169,7 +1176,7 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     if (pair)
         k_tc_selftest_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl);
     else
-        k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl);
+        k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl, stall_kb);
     TRY(cudaGetLastError());
     TRY(cudaDeviceSynchronize());
     Ctl h;

@@ -826,6 +826,21 @@ int panda_set_profiling(panda_ctx *c, int on)
 
 int panda_kernel_count(const panda_ctx *c) { return c ? n_kernels(c) : 0; }
 
+int panda_selftest_timeout(void)
+{
+    if (!tc_supported())
+        return set_err(nullptr, PANDA_EUNSUPPORTED, "panda_selftest_timeout: needs an sm_103 device");
+    const int M = 128, N = 128, K = 256;
+    std::vector<float> A((size_t)M * K, 1.0f), B((size_t)N * K, 1.0f), D((size_t)M * N, 0.0f);
+    int status = 0;
+    cudaError_t e = tc_selftest_gemm(M, N, K, A.data(), B.data(), D.data(), 1, 0, 0, &status);
+    if (e != cudaSuccess)
+        return set_err(nullptr, PANDA_ECUDA, std::string("panda_selftest_timeout: ") + cudaGetErrorString(e));
+    if (status & ST_TIMEOUT)
+        return set_err(nullptr, PANDA_ETIMEOUT, "panda_selftest_timeout: the planted wait expired as intended");
+    return 0;
+}
+
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms)
 {
     // terms + 10: the same product on CTA pairs (cta_group::2, 256 x 256 tiles)
@@ -836,7 +851,7 @@ int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, 
     if (!tc_supported())
         return set_err(nullptr, PANDA_EUNSUPPORTED, "panda_selftest_tc_gemm: needs an sm_103 device");
     int status = 0;
-    cudaError_t e = tc_selftest_gemm(M, N, K, A, B, D, terms, pair, &status);
+    cudaError_t e = tc_selftest_gemm(M, N, K, A, B, D, terms, pair, -1, &status);
     if (e != cudaSuccess)
         return set_err(nullptr, PANDA_ECUDA, std::string("panda_selftest_tc_gemm: ") + cudaGetErrorString(e));
     if (status & ST_TIMEOUT)

@@ -120,7 +120,8 @@ void tc_release(Dev &d);
 cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
 // D (M x N, row-major) = A (M x K) . B (N x K)^T through the tcgen05 pipeline,
 // host buffers; terms = 1 (hi only) or 3 (split).  *status: device status bits.
+// stall_kb >= 0 plants a stage whose loads are never issued (timeout test).
 cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms,
-                             int pair, int *status);
+                             int pair, int stall_kb, int *status);
 
 }  // namespace panda

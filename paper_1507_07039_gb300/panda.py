@@ -66,6 +66,7 @@ def _load() -> ctypes.CDLL:
         "panda_precision_supported": (i, [i]),
         "panda_step_static": (i, [i, i, vp, vp, vp, f, i, i, pd, vp]),
         "panda_selftest_tc_gemm": (i, [i, i, i, vp, vp, vp, i]),
+        "panda_selftest_timeout": (i, []),
         "panda_batch_create": (i, [pvp, i, pi, pi, pvp, pvp, pvp, popts]),
         "panda_batch_run": (i, [vp, f, d, i, pi, pd]),
         "panda_batch_get": (i, [vp, i, vp, vp, vp]),
@@ -256,6 +257,11 @@ def panda_selftest_tc_gemm(A, B, terms: int = 3) -> np.ndarray:
     D = np.empty((M, N), np.float32)
     _check(lib.panda_selftest_tc_gemm(M, N, K, _ptr(A), _ptr(B), _ptr(D), int(terms)))
     return D
+
+
+def panda_selftest_timeout() -> int:
+    """Return code of the planted-timeout self-test (PANDA_ETIMEOUT = -7 expected)."""
+    return int(lib.panda_selftest_timeout())
 
 
 PANDA_STATIC_MAX_NODES = 512

@@ -66,3 +66,19 @@ def test_cta_pair_product(M, N, K):
     D3 = panda.panda_selftest_tc_gemm(A, B, terms=13)
     ref3 = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
     assert np.max(np.abs(D3 - ref3)) / scale < 1e-5
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable():
+    """A pipeline stage armed but never loaded: the kernel's bounded waits
+    must end it with PANDA_ETIMEOUT (about a second), not hang; the next
+    product on the same device is still right."""
+    import time
+    from paper_1507_07039_gb300 import panda
+    t0 = time.time()
+    rc = panda.panda_selftest_timeout()
+    assert rc == -7, (rc, panda.panda_last_error(None))
+    assert time.time() - t0 < 30
+    A = np.ones((128, 64), np.float32)
+    B = np.full((128, 64), 2.0, np.float32)
+    D = panda.panda_selftest_tc_gemm(A, B, terms=1)
+    assert np.all(D == 128.0)
