@@ -67,6 +67,14 @@ __device__ __forceinline__ float tanimoto_fast(float num, float nx, float ny)
     return den > 0.0f ? num * rsqrtf(den) : 0.0f;
 }
 
+// As tanimoto_fast without the branch: the denominator is at least
+// (|x|^2 + |y|^2)/2 > 0 unless both vectors are zero, in which case the
+// numerator is 0 too and the clamp keeps the result 0.
+__device__ __forceinline__ float tanimoto_clamped(float num, float nx, float ny)
+{
+    return num * rsqrtf(fmaxf((nx + ny) - fabsf(num), 1e-30f));
+}
+
 // hi / lo of a whole array (padding stays zero because x is zero there)
 __global__ void k_split(const float *__restrict__ X, size_t n, __nv_bfloat16 *__restrict__ H,
                         __nv_bfloat16 *__restrict__ L)
@@ -575,27 +583,28 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
 // the even CTA issues cta_group::2 MMAs (M = N = 256) whose result rows
 // 128 r .. + 127 land in CTA r's TMEM.  Two accumulators of 256 columns
 // alternate, so the epilogue of one tile overlaps the MMAs of the next.
-// Warps: 0 TMA, 1 MMA (even CTA), 2-9 epilogue (two per TMEM lane quarter,
-// each taking 128 of the 256 columns in 16-column sub-chunks).
+// Warps: 0 TMA, 1 MMA (even CTA), then EPI2 epilogue warps (EPI2 / 4 per
+// TMEM lane quarter, splitting the 256 columns in 16-column sub-chunks).
 //
 // Row partial sums for Eq. 6 use separate slot ranges so the two CTAs of a
 // pair never exchange data: the row role (a row of the tile, summed over its
 // 256 columns) goes to slot bn, the column role (a column of the tile, summed
 // over this CTA's 128 rows) to slot nb + 2 bm + r.
 // ---------------------------------------------------------------------------
-constexpr int EPI2 = 8;
+constexpr int EPI2 = 8;                    // epilogue warps: EPI2 / 4 per TMEM lane quarter
 constexpr int THREADS2 = 64 + 32 * EPI2;
 constexpr int N2 = 256;                    // tile edge
 constexpr uint32_t STAGE2 = 4 * A_BYTES;   // per CTA: A hi, A lo, B hi, B lo (128 rows each)
 
-// Rule D2 keeps three partial sums per row instead of two and so runs with one
-// stage fewer to fit its larger reduction buffers.
+// named barrier among the phase-2 epilogue warps
+__device__ __forceinline__ void epi_bar_p2() { asm volatile("bar.sync 2, %0;" ::"n"(32 * EPI2) : "memory"); }
+
 template <bool SIM>
 struct P2Cfg {
     static constexpr int NS = SIM ? 3 : 2;             // sums per row: x, x^2 (and v^2 under D2)
-    static constexpr int ST = SIM ? 2 : 3;             // pipeline stages
+    static constexpr int ST = EPI2 > 8 || SIM ? 2 : 3;  // pipeline stages that fit beside the epilogue buffers
     static constexpr size_t COLRED = 4 * NS * N2;      // [quarter][sum][column] floats
-    static constexpr size_t ROWRED = 2 * NS * 128;     // [half][sum][row] floats
+    static constexpr size_t ROWRED = (EPI2 / 4) * NS * 128;  // [column part][sum][row] floats
     static constexpr size_t COLNRM = N2;               // the tile's column norms
     static constexpr size_t BLK = 32 * 17;             // per epilogue warp: 32 x 16 staging block (padded)
 };
@@ -728,10 +737,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             sy.consumed = g;
         }
     } else {  // ---- epilogue: warps 2..9 of both CTAs ----
-        const int e = warp - 2, wq = warp & 3, half = e >> 2;
+        // the EPI2 / 4 warps of a lane quarter split its 16 sub-chunks of 16 columns
+        constexpr int PARTS = EPI2 / 4;
+        const int e = warp - 2, wq = warp & 3, third = e >> 2;
+        const int c_begin = (16 * third) / PARTS, c_end = (16 * (third + 1)) / PARTS;
         const int r = wq * 32 + lane;  // row of this CTA's 128-row half
         float *blk = blocks + (size_t)e * Cfg::BLK;  // this warp's 32 x 16 staging block, rows of 17
-        const int tt = threadIdx.x - 64;  // 0..255
+        const int tt = threadIdx.x - 64;  // 0..383
         const float a = ctl->alpha, keep = 1.0f - a;
         const uint32_t tempty_even = mapa_shared(smem_u32(&sy.tempty[0]), 0);
         for (int n = first, idx = 0; n < last; ++n, ++idx) {
@@ -747,40 +759,38 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             const int buf = idx & 1;
             // everything that does not depend on the accumulator is fetched before waiting for it:
             // the tile's column norms (shared), this row's norm and its first old values
-            colnrm[tt] = n0 + tt < nn ? nrm[n0 + tt] : 0.0f;
+            if (tt < N2)
+                colnrm[tt] = n0 + tt < nn ? nrm[n0 + tt] : 0.0f;
             const int k = m0 + r, k0 = m0 + wq * 32;
             const bool krow = k < nn;  // rows past the network (last block's padding) hold nothing
             const float nk_ = krow ? nrm[k] : 0.0f;
-            const float *xrow = X + (size_t)(krow ? k : 0) * ld + n0 + half * 128;
+            const float *xrow = X + (size_t)(krow ? k : 0) * ld + n0;
             float nxt[16];
-            if (krow && n0 + half * 128 < ld)
-                ld16(xrow, nxt);
-            epi_bar2();
+            if (krow && n0 + c_begin * 16 < ld)
+                ld16(xrow + c_begin * 16, nxt);
+            epi_bar_p2();
             // on a timed-out wait every epilogue warp still runs the named barriers below
             const bool live = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, ctl) &&
                               !*(volatile int *)&sy.abort;
             tc_fence_after();
             float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
-            const uint32_t tbase = sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16) + half * 128;
-            uint32_t accn[16];
-            if (live) {
-                tmem_ld16_nowait(tbase, accn);
-                tmem_wait();
-            }
+            const uint32_t tbase = sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16);
 #pragma unroll 1
-            for (int c = 0; c < 8 && live; ++c) {  // eight 16-column sub-chunks of this warp's 128 columns
-                const int cc = half * 128 + c * 16, j0 = n0 + cc;
+            for (int c = c_begin; c < c_end && live; ++c) {  // this warp's 16-column sub-chunks
+                const int cc = c * 16, j0 = n0 + cc;
                 const bool inside = krow && j0 < ld;
                 float old[16], acc[16];
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
+                for (int q = 0; q < 16; ++q)
                     old[q] = inside ? nxt[q] : 0.0f;
-                    acc[q] = __uint_as_float(accn[q]);
-                }
-                if (c < 7) {
-                    if (krow && j0 + 16 < ld)
-                        ld16(xrow + (c + 1) * 16, nxt);      // next sub-chunk's old values and
-                    tmem_ld16_nowait(tbase + (c + 1) * 16, accn);  // accumulator, in flight meanwhile
+                if (c + 1 < c_end && krow && j0 + 16 < ld)
+                    ld16(xrow + (c + 1) * 16, nxt);  // next sub-chunk's old values, in flight meanwhile
+                tmem_ld16(tbase + cc, acc);
+                if (c + 1 == c_end) {  // this warp is done with the accumulator: tell the even CTA
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive_cluster(tempty_even + buf * (uint32_t)sizeof(uint64_t));
                 }
                 // interior sub-chunks of off-diagonal tiles are entirely valid
                 uint32_t vmask = 0xffffu;
@@ -790,24 +800,39 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                     for (int q = 0; q < 16; ++q)
                         vmask |= (k < j0 + q && j0 + q < nn) ? (1u << q) : 0u;
                 }
-                float nj[16];
+                if (vmask == 0xffffu) {  // interior: no masking
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 v4 = reinterpret_cast<const float4 *>(colnrm + cc)[q];
-                    nj[4 * q] = v4.x; nj[4 * q + 1] = v4.y; nj[4 * q + 2] = v4.z; nj[4 * q + 3] = v4.w;
-                }
+                    for (int q = 0; q < 4; ++q) {
+                        const float4 n4 = reinterpret_cast<const float4 *>(colnrm + cc)[q];
+                        const float nj[4] = {n4.x, n4.y, n4.z, n4.w};
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const float s = tanimoto_fast(acc[q], nk_, nj[q]);
-                    const bool valid = (vmask >> q) & 1u;
-                    const float v = valid ? fmaf(a, s, keep * old[q]) : old[q];
-                    const float x = valid ? (SIM_SIGMA ? s : v) : 0.0f;
-                    r1 += x;
-                    r2 += x * x;
-                    if (SIM_SIGMA)
-                        rv += valid ? v * v : 0.0f;
-                    old[q] = v;
-                    acc[q] = x;
+                        for (int u = 0; u < 4; ++u) {
+                            const int e2 = 4 * q + u;
+                            const float s = tanimoto_clamped(acc[e2], nk_, nj[u]);
+                            const float v = fmaf(a, s, keep * old[e2]);
+                            const float x = SIM_SIGMA ? s : v;
+                            r1 += x;
+                            r2 = fmaf(x, x, r2);
+                            if (SIM_SIGMA)
+                                rv = fmaf(v, v, rv);
+                            old[e2] = v;
+                            acc[e2] = x;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        const float s = tanimoto_fast(acc[q], nk_, colnrm[cc + q]);
+                        const bool valid = (vmask >> q) & 1u;
+                        const float v = valid ? fmaf(a, s, keep * old[q]) : old[q];
+                        const float x = valid ? (SIM_SIGMA ? s : v) : 0.0f;
+                        r1 += x;
+                        r2 += x * x;
+                        if (SIM_SIGMA)
+                            rv += valid ? v * v : 0.0f;
+                        old[q] = v;
+                        acc[q] = x;
+                    }
                 }
                 // column sums of s under D2 (from registers; v sums come from the staged block)
                 if (SIM_SIGMA) {
@@ -890,19 +915,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                     }
                 }
                 __syncwarp();  // the block is rewritten by the next sub-chunk
-                tmem_wait();   // the next sub-chunk's accumulator has landed
-                if (c == 6) {  // that was the last load from this accumulator: tell the even CTA
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0)
-                        mbar_arrive_cluster(tempty_even + buf * (uint32_t)sizeof(uint64_t));
-                }
             }
-            rowred[(half * NS + 0) * 128 + r] = r1;
-            rowred[(half * NS + 1) * 128 + r] = r2;
+            rowred[(third * NS + 0) * 128 + r] = r1;
+            rowred[(third * NS + 1) * 128 + r] = r2;
             if (SIM_SIGMA)
-                rowred[(half * NS + 2) * 128 + r] = rv;
-            epi_bar2();
+                rowred[(third * NS + 2) * 128 + r] = rv;
+            epi_bar_p2();
             if (live) {
 #pragma unroll
                 for (int w = 0; w < 3; ++w) {
@@ -910,17 +928,21 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                                                                             : (isP ? d.ps_vsq : d.cs_vsq);
                     const int wc = (!SIM_SIGMA && w == 2) ? 1 : w;  // sum of v^2 = sum of x^2 unless D2
                     // column role: tile column tt, summed over this CTA's 128 rows
-                    const float cs = ((colred[(0 * NS + wc) * N2 + tt] + colred[(1 * NS + wc) * N2 + tt]) +
-                                      colred[(2 * NS + wc) * N2 + tt]) + colred[(3 * NS + wc) * N2 + tt];
-                    if (n0 + tt < ld)
-                        S[(size_t)(nbk + 2 * bm + (int)rank) * ld + n0 + tt] = cs;
+                    if (tt < N2 && n0 + tt < ld)
+                        S[(size_t)(nbk + 2 * bm + (int)rank) * ld + n0 + tt] =
+                            ((colred[(0 * NS + wc) * N2 + tt] + colred[(1 * NS + wc) * N2 + tt]) +
+                             colred[(2 * NS + wc) * N2 + tt]) + colred[(3 * NS + wc) * N2 + tt];
                     // row role: tile row tt of this CTA, summed over the 256 columns
-                    if (tt < 128 && m0 + tt < ld)
-                        S[(size_t)bn * ld + m0 + tt] =
-                            rowred[(0 * NS + wc) * 128 + tt] + rowred[(1 * NS + wc) * 128 + tt];
+                    if (tt < 128 && m0 + tt < ld) {
+                        float rs = 0.0f;
+#pragma unroll
+                        for (int pp = 0; pp < PARTS; ++pp)
+                            rs += rowred[(pp * NS + wc) * 128 + tt];
+                        S[(size_t)bn * ld + m0 + tt] = rs;
+                    }
                 }
             }
-            epi_bar2();
+            epi_bar_p2();
         }
     }
     tc_fence_before();
