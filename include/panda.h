@@ -165,7 +165,10 @@ int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, do
  * uses.  A is M x K, B is N x K, D is M x N, all row-major FP32 host buffers;
  * each operand is split into BF16 hi + lo and terms = 3 sums hi*hi + hi*lo +
  * lo*hi, terms = 1 uses hi*hi only; terms + 10 runs the same product on CTA
- * pairs (cta_group::2 MMAs over 256 x 256 tiles).  PANDA_EUNSUPPORTED off
+ * pairs (cta_group::2 MMAs over 256 x 256 tiles); terms + 20 does so with B
+ * held transposed on the device ([K][N]) and fed to the MMAs MN-major, the
+ * form the availability product reads the lower triangle of C in.
+ * PANDA_EINVAL on other terms or non-positive sizes; PANDA_EUNSUPPORTED off
  * sm_103. */
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms);
 

@@ -1,23 +1,29 @@
-// BF16X3 tensor-core path of one PANDA iteration (sm_103a, tcgen05 + TMA).
+// BF16X3 tensor-core path of one PANDA iteration (sm_103a, tcgen05 + TMA),
+// every GEMM tile on a CTA pair (cta_group::2, 256 x 256 outputs).
 //
-//   k_tc_phase1   per 128 x BN1 tile of W': two TMEM accumulators,
+//   k_tc_phase1   per 256 (TFs) x 256 (genes) tile of W': two TMEM accumulators,
 //                   R-num = P_off . W   (K = TFs;   A = P_off rows, B = W^T rows)
 //                   A-num = W . C_off   (K = genes; A = W rows,     B = C_off rows)
 //                 then the fused epilogue of Eqs. 1-3 and 2: diagonal terms,
 //                 Tanimoto, damped W update, h and norm partials, and the
 //                 FP32 W' plus its split copies in both orientations.
 //   k_reduce_wnorms  (shared with the FP32 path)
-//   k_tc_phase2   persistent: upper-triangle 128 x 128 tiles of W'.W'^T (P,
+//   k_tc_phase2   persistent: upper-triangle 256 x 256 tiles of W'.W'^T (P,
 //                 K = genes) and W'^T.W' (C, K = TFs) from a balanced host-built
 //                 schedule, double-buffered TMEM accumulators, and the Eq. 5
 //                 epilogue: Tanimoto, damped update, the FP32 upper triangle,
-//                 split copies of both triangles, row partial sums for Eq. 6.
-//                 (Only the upper triangle of FP32 P and C is ever read here;
-//                 panda_get and panda_save mirror it first.)
+//                 split copies of the upper triangle (of P: both triangles; of
+//                 C: both only inside diagonal 256-blocks), row partial sums
+//                 for Eq. 6.  (Only the upper triangle of FP32 P and C is ever
+//                 read here; panda_get and panda_save mirror it first.)
 //   k_fin, k_tail (shared): Eq. 6 diagonals, norms, h, stop test.
 //
-// C and P are symmetric, so "C_off rows" and "P_off rows" are the K-major
-// layouts the B and A operands need.
+// P and C are symmetric.  "P_off rows" are read K-major from the full split
+// copy.  For "C_off rows" j against genes k, the availability product reads
+// C_off[j][k] K-major where k lies at or past the tile's diagonal 256-block
+// (upper triangle and diagonal blocks), and as C_off[k][j], rows k of the
+// upper triangle loaded MN-major, where k lies before it: the split copy of
+// C's lower triangle outside the diagonal blocks is never written or read.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -44,6 +50,7 @@ struct TcMaps {  // split copies, K-major, boxes of 64 x 128 (one CTA's half of 
     CUtensorMap Wh[2], Wl[2];        // W split       [Tp][Gp]
     CUtensorMap Wth[2], Wtl[2];      // W^T split     [Gp][Tp]
     CUtensorMap Ch, Cl;              // C_off split   [Gp][Gp]
+    CUtensorMap Chm, Clm;            // the same arrays in boxes of 64 x 64, for MN-major loads
 };
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
@@ -223,7 +230,7 @@ struct SyncPair {
 };
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
-    k_tc_selftest_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl)
+    k_tc_selftest_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl, int bmn)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
@@ -261,14 +268,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                 uint8_t *st = stages + (size_t)s * PAIR_STAGE;
                 tma_load_2d_pair(st, &maps.Ah, fb, kb * BK, m0 + 128 * rank);
                 tma_load_2d_pair(st + A_BYTES, &maps.Al, fb, kb * BK, m0 + 128 * rank);
-                tma_load_2d_pair(st + 2 * A_BYTES, &maps.Bh, fb, kb * BK, n0 + 128 * rank);
-                tma_load_2d_pair(st + 3 * A_BYTES, &maps.Bl, fb, kb * BK, n0 + 128 * rank);
+                if (bmn) {  // B^T stored [K][N]: two 64 x 64 boxes per CTA half, N contiguous
+                    for (int h = 0; h < 2; ++h) {
+                        tma_load_2d_pair(st + 2 * A_BYTES + h * (A_BYTES / 2), &maps.Bh, fb,
+                                         n0 + 128 * rank + 64 * h, kb * BK);
+                        tma_load_2d_pair(st + 3 * A_BYTES + h * (A_BYTES / 2), &maps.Bl, fb,
+                                         n0 + 128 * rank + 64 * h, kb * BK);
+                    }
+                } else {
+                    tma_load_2d_pair(st + 2 * A_BYTES, &maps.Bh, fb, kb * BK, n0 + 128 * rank);
+                    tma_load_2d_pair(st + 3 * A_BYTES, &maps.Bl, fb, kb * BK, n0 + 128 * rank);
+                }
             }
             sy.issued = kb;
         }
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {  // the even CTA issues the pair's MMAs
-            constexpr uint32_t idesc = idesc_bf16_f32(256, PAIR_N);
+            const uint32_t idesc = idesc_bf16_f32(256, PAIR_N) | (bmn ? IDESC_B_MN : 0u);
             int kb = 0;
             for (; kb < nk; ++kb) {
                 const int s = kb % PAIR_ST;
@@ -281,8 +297,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                 for (int kk = 0; kk < BK / 16; ++kk) {
                     const uint32_t off = kk * 32;
                     const uint64_t ah = sdesc_k_sw128(base + off), al = sdesc_k_sw128(base + A_BYTES + off);
-                    const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
-                    const uint64_t bl = sdesc_k_sw128(base + 3 * A_BYTES + off);
+                    const uint64_t bh = bmn ? sdesc_mn_sw128(base + 2 * A_BYTES + kk * 2048, A_BYTES / 2)
+                                            : sdesc_k_sw128(base + 2 * A_BYTES + off);
+                    const uint64_t bl = bmn ? sdesc_mn_sw128(base + 3 * A_BYTES + kk * 2048, A_BYTES / 2)
+                                            : sdesc_k_sw128(base + 3 * A_BYTES + off);
                     mma_bf16_pair(sy.tmem, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
                     mma_bf16_pair(sy.tmem, ah, bl, idesc, 1u);
                     mma_bf16_pair(sy.tmem, al, bh, idesc, 1u);
@@ -412,8 +430,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                     const int k = (kb - nR) * BK;
                     tma_load_2d_pair(b, &maps.Wh[cur], fb, k, m0);
                     tma_load_2d_pair(b + A_BYTES, &maps.Wl[cur], fb, k, m0);
-                    tma_load_2d_pair(b + 2 * A_BYTES, &maps.Ch, fb, k, nb0);
-                    tma_load_2d_pair(b + 3 * A_BYTES, &maps.Cl, fb, k, nb0);
+                    if (k >= n0) {  // C_off[j][k], k at or past the tile's diagonal block: stored rows
+                        tma_load_2d_pair(b + 2 * A_BYTES, &maps.Ch, fb, k, nb0);
+                        tma_load_2d_pair(b + 3 * A_BYTES, &maps.Cl, fb, k, nb0);
+                    } else {        // k < j: C_off[j][k] = C_off[k][j], rows k of the upper triangle
+                        for (int h = 0; h < 2; ++h) {
+                            tma_load_2d_pair(b + 2 * A_BYTES + h * (A_BYTES / 2), &maps.Chm, fb, nb0 + 64 * h, k);
+                            tma_load_2d_pair(b + 3 * A_BYTES + h * (A_BYTES / 2), &maps.Clm, fb, nb0 + 64 * h, k);
+                        }
+                    }
                 }
             }
             sy.issued = kb;
@@ -430,16 +455,20 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                 const uint32_t base = smem_u32(stages + (size_t)st * STAGE1);
                 const uint32_t dacc = sy.tmem + (kb < nR ? 0u : 256u);
                 const bool fresh = kb == 0 || kb == nR;
+                const bool bmn = kb >= nR && (kb - nR) * BK < n0;  // B block loaded MN-major
+                const uint32_t id = bmn ? (idesc | IDESC_B_MN) : idesc;
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
                     const uint32_t off = kk * 32;
                     const uint64_t ah = sdesc_k_sw128(base + off);
                     const uint64_t al = sdesc_k_sw128(base + A_BYTES + off);
-                    const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
-                    const uint64_t bl = sdesc_k_sw128(base + 3 * A_BYTES + off);
-                    mma_bf16_pair(dacc, ah, bh, idesc, (fresh && kk == 0) ? 0u : 1u);
-                    mma_bf16_pair(dacc, ah, bl, idesc, 1u);
-                    mma_bf16_pair(dacc, al, bh, idesc, 1u);
+                    const uint64_t bh = bmn ? sdesc_mn_sw128(base + 2 * A_BYTES + kk * 2048, A_BYTES / 2)
+                                            : sdesc_k_sw128(base + 2 * A_BYTES + off);
+                    const uint64_t bl = bmn ? sdesc_mn_sw128(base + 3 * A_BYTES + kk * 2048, A_BYTES / 2)
+                                            : sdesc_k_sw128(base + 3 * A_BYTES + off);
+                    mma_bf16_pair(dacc, ah, bh, id, (fresh && kk == 0) ? 0u : 1u);
+                    mma_bf16_pair(dacc, ah, bl, id, 1u);
+                    mma_bf16_pair(dacc, al, bh, id, 1u);
                 }
                 mma_commit_pair(&sy.empty[st]);
             }
@@ -756,6 +785,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             const float *nrm = isP ? d.rsqW : d.csqW;
             float *X = isP ? d.Poff : d.Coff;
             __nv_bfloat16 *Xh = isP ? d.Ph : d.Ch, *Xl = isP ? d.Pl : d.Cl;
+            // split copies of the lower triangle: all of P (phase 1 reads its rows K-major), but of C
+            // only inside diagonal 256-blocks (phase 1 reads the rest of C's lower triangle MN-major)
+            const bool mirror = isP || bm == bn;
             const int buf = idx & 1;
             // everything that does not depend on the accumulator is fetched before waiting for it:
             // the tile's column norms (shared), this row's norm and its first old values
@@ -901,17 +933,19 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                             colred[(wq * NS + 1) * N2 + cc + lane] = c2;
                         }
                     }
-                    uint32_t hv[8], lv[8];
+                    if (mirror) {
+                        uint32_t hv[8], lv[8];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        split_pair(g[2 * q], g[2 * q + 1], hv[q], lv[q]);
-                    const int jm = j0 + col, km = k0 + h16;
-                    const uint32_t mmask =
-                        jm >= nn ? 0u : (km + 15 < jm ? 0xffffu : (km >= jm ? 0u : ((1u << (jm - km)) - 1u)));
-                    if (mmask) {
-                        const size_t mo = (size_t)jm * ld + km;
-                        st16_packed(Xh + mo, hv, mmask);
-                        st16_packed(Xl + mo, lv, mmask);
+                        for (int q = 0; q < 8; ++q)
+                            split_pair(g[2 * q], g[2 * q + 1], hv[q], lv[q]);
+                        const int jm = j0 + col, km = k0 + h16;
+                        const uint32_t mmask =
+                            jm >= nn ? 0u : (km + 15 < jm ? 0xffffu : (km >= jm ? 0u : ((1u << (jm - km)) - 1u)));
+                        if (mmask) {
+                            const size_t mo = (size_t)jm * ld + km;
+                            st16_packed(Xh + mo, hv, mmask);
+                            st16_packed(Xl + mo, lv, mmask);
+                        }
                     }
                 }
                 __syncwarp();  // the block is rewritten by the next sub-chunk
@@ -978,6 +1012,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 // 128-byte swizzle.
 cudaError_t make_map(CUtensorMap *m, const void *base, int rows, int cols, int box_rows)
 {
+    // box: 64 columns (128 B, the swizzle span) by box_rows rows
     auto fn = encode_fn();
     if (!fn)
         return cudaErrorNotSupported;
@@ -1095,7 +1130,8 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s)
         std::memset(m, 0, sizeof *m);
         d.tc_host = h;
         if ((e = make_map(&m->Ph, d.Ph, d.Tp, d.Tp, 128)) || (e = make_map(&m->Pl, d.Pl, d.Tp, d.Tp, 128)) ||
-            (e = make_map(&m->Ch, d.Ch, d.Gp, d.Gp, 128)) || (e = make_map(&m->Cl, d.Cl, d.Gp, d.Gp, 128)))
+            (e = make_map(&m->Ch, d.Ch, d.Gp, d.Gp, 128)) || (e = make_map(&m->Cl, d.Cl, d.Gp, d.Gp, 128)) ||
+            (e = make_map(&m->Chm, d.Ch, d.Gp, d.Gp, 64)) || (e = make_map(&m->Clm, d.Cl, d.Gp, d.Gp, 64)))
             return e;
         for (int b = 0; b < 2; ++b)
             if ((e = make_map(&m->Wh[b], d.Wh[b], d.Tp, d.Gp, 128)) ||
@@ -1182,7 +1218,15 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     TRY(cudaMemset(dA, 0, (size_t)Mp * Kp * 4));
     TRY(cudaMemset(dB, 0, (size_t)Np * Kp * 4));
     TRY(cudaMemcpy2D(dA, (size_t)Kp * 4, A, (size_t)K * 4, (size_t)K * 4, M, cudaMemcpyHostToDevice));
-    TRY(cudaMemcpy2D(dB, (size_t)Kp * 4, B, (size_t)K * 4, (size_t)K * 4, N, cudaMemcpyHostToDevice));
+    if (pair == 2) {  // B^T, [Kp][Np], for the MN-major B loads
+        std::vector<float> bt((size_t)K * N);
+        for (int n = 0; n < N; ++n)
+            for (int k = 0; k < K; ++k)
+                bt[(size_t)k * N + n] = B[(size_t)n * K + k];
+        TRY(cudaMemcpy2D(dB, (size_t)Np * 4, bt.data(), (size_t)N * 4, (size_t)N * 4, K, cudaMemcpyHostToDevice));
+    } else {
+        TRY(cudaMemcpy2D(dB, (size_t)Kp * 4, B, (size_t)K * 4, (size_t)K * 4, N, cudaMemcpyHostToDevice));
+    }
     k_split<<<256, 256>>>(dA, (size_t)Mp * Kp, Ah, Al);
     k_split<<<256, 256>>>(dB, (size_t)Np * Kp, Bh, Bl);
     TRY(cudaGetLastError());
@@ -1192,11 +1236,17 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     }
     TRY(make_map(&maps.Ah, Ah, Mp, Kp, 128));
     TRY(make_map(&maps.Al, Al, Mp, Kp, 128));
-    TRY(make_map(&maps.Bh, Bh, Np, Kp, 128));
-    TRY(make_map(&maps.Bl, Bl, Np, Kp, 128));
+    if (pair == 2) {
+        TRY(make_map(&maps.Bh, Bh, Kp, Np, 64));
+        TRY(make_map(&maps.Bl, Bl, Kp, Np, 64));
+    } else {
+        TRY(make_map(&maps.Bh, Bh, Np, Kp, 128));
+        TRY(make_map(&maps.Bl, Bl, Np, Kp, 128));
+    }
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
     if (pair)
-        k_tc_selftest_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl);
+        k_tc_selftest_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl,
+                                                                                    pair == 2);
     else
         k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl, stall_kb);
     TRY(cudaGetLastError());

@@ -843,9 +843,12 @@ int panda_selftest_timeout(void)
 
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms)
 {
-    // terms + 10: the same product on CTA pairs (cta_group::2, 256 x 256 tiles)
-    const int pair = terms >= 10;
+    // terms + 10: the same product on CTA pairs (cta_group::2, 256 x 256 tiles);
+    // terms + 20: on CTA pairs with B stored transposed and loaded MN-major
+    const int pair = terms / 10;
     terms %= 10;
+    if (pair > 2)
+        return set_err(nullptr, PANDA_EINVAL, "panda_selftest_tc_gemm: bad argument");
     if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !D || (terms != 1 && terms != 3))
         return set_err(nullptr, PANDA_EINVAL, "panda_selftest_tc_gemm: bad argument");
     if (!tc_supported())

@@ -129,6 +129,27 @@ __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr)
     return d;
 }
 
+// Shared-memory matrix descriptor of an MN-major tile with the 128-byte
+// swizzle, as TMA writes a box of 64 MN-contiguous elements by K rows: each K
+// row is 128 B (64 BF16 along M or N), 8 rows form a 1024-B swizzle atom.
+// Leading offset (bits 16-29) = byte stride between atoms along MN (the next
+// 64 elements), stride offset (bits 32-45) = byte stride between 8-row groups
+// along K (1024 B); both >> 4.  One MMA of K = 16 spans two K groups, so the
+// start address advances by 2048 B per step along K.
+__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t mn_atom_bytes)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((mn_atom_bytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction-descriptor bit that marks the B operand MN-major ("transpose B").
+constexpr uint32_t IDESC_B_MN = 1u << 16;
+
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major: D format (bits 4-5) = F32, A format (7-9) = BF16,
 // B format (10-12) = BF16, N >> 3 (17-22), M >> 4 (24-28).

@@ -68,6 +68,27 @@ def test_cta_pair_product(M, N, K):
     assert np.max(np.abs(D3 - ref3)) / scale < 1e-5
 
 
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (300, 600, 1000), (512, 256, 130)])
+def test_cta_pair_product_mn_major_b(M, N, K):
+    """CTA pairs with B held transposed ([K][N], N contiguous) and fed to the
+    MMAs MN-major: the same products as the K-major form."""
+    from paper_1507_07039_gb300 import panda
+    rng = np.random.default_rng(5 * M + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    Ah, Al = bf16_split(A)
+    Bh, Bl = bf16_split(B)
+    D1 = panda.panda_selftest_tc_gemm(A, B, terms=21)
+    ref1 = Ah @ Bh.T
+    scale = max(1.0, np.max(np.abs(ref1)))
+    assert np.max(np.abs(D1 - ref1)) / scale < 2e-6
+    D3 = panda.panda_selftest_tc_gemm(A, B, terms=23)
+    ref3 = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
+    assert np.max(np.abs(D3 - ref3)) / scale < 1e-5
+    # the K-major form of the same pair kernel gives the same sums up to accumulation order
+    assert np.max(np.abs(D3 - panda.panda_selftest_tc_gemm(A, B, terms=13))) / scale < 1e-5
+
+
 def test_bounded_wait_reports_timeout_and_device_stays_usable():
     """A pipeline stage armed but never loaded: the kernel's bounded waits
     must end it with PANDA_ETIMEOUT (about a second), not hang; the next
