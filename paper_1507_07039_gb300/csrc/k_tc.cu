@@ -109,6 +109,14 @@ __device__ __forceinline__ void ld16(const float *src, float (&v)[16])
     }
 }
 
+// four float4 at p, p + 8 ld, p + 16 ld, p + 24 ld (a warp's coalesced 32-row x 16-column block)
+__device__ __forceinline__ void ld_rows4(const float *p, int ld, float4 (&v)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        v[i] = *reinterpret_cast<const float4 *>(p + (size_t)(8 * i) * ld);
+}
+
 // 16 BF16 values held as 8 packed pairs: two 16-byte stores, or the masked entries
 __device__ __forceinline__ void st16_packed(__nv_bfloat16 *dst, const uint32_t (&p)[8], uint32_t mask)
 {
@@ -796,10 +804,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             const int k = m0 + r, k0 = m0 + wq * 32;
             const bool krow = k < nn;  // rows past the network (last block's padding) hold nothing
             const float nk_ = krow ? nrm[k] : 0.0f;
-            const float *xrow = X + (size_t)(krow ? k : 0) * ld + n0;
-            float nxt[16];
-            if (krow && n0 + c_begin * 16 < ld)
-                ld16(xrow + c_begin * 16, nxt);
+            // old values, loaded coalesced (8 rows x 64 B per load): lane l takes columns
+            // 4 (l & 3) .. + 3 of the warp's rows (l >> 2) + 8 i, i = 0..3 (rows past the network
+            // are padding inside the array; their values are never used)
+            const float *xblk = X + (size_t)(k0 + (lane >> 2)) * ld + n0 + 4 * (lane & 3);
+            float4 nxt[4];
+            if (n0 + c_begin * 16 < ld)
+                ld_rows4(xblk + c_begin * 16, ld, nxt);
             epi_bar_p2();
             // on a timed-out wait every epilogue warp still runs the named barriers below
             const bool live = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, ctl) &&
@@ -807,17 +818,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             tc_fence_after();
             float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
             const uint32_t tbase = sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16);
+            // accumulator columns one sub-chunk ahead: each sub-chunk's TMEM load is issued once the
+            // previous one's arithmetic is done and lands while that one's stores go out
+            uint32_t accr[16];
+            if (live)
+                tmem_ld16_nowait(tbase + c_begin * 16, accr);
 #pragma unroll 1
             for (int c = c_begin; c < c_end && live; ++c) {  // this warp's 16-column sub-chunks
                 const int cc = c * 16, j0 = n0 + cc;
                 const bool inside = krow && j0 < ld;
                 float old[16], acc[16];
+                // old values to this lane's own row through the staging block
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float *b = blk + ((lane >> 2) + 8 * i) * 17 + 4 * (lane & 3);
+                    b[0] = nxt[i].x; b[1] = nxt[i].y; b[2] = nxt[i].z; b[3] = nxt[i].w;
+                }
+                __syncwarp();
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    old[q] = inside ? nxt[q] : 0.0f;
-                if (c + 1 < c_end && krow && j0 + 16 < ld)
-                    ld16(xrow + (c + 1) * 16, nxt);  // next sub-chunk's old values, in flight meanwhile
-                tmem_ld16(tbase + cc, acc);
+                    old[q] = inside ? blk[lane * 17 + q] : 0.0f;
+                __syncwarp();  // the block takes the new values next
+                if (c + 1 < c_end && j0 + 16 < ld)
+                    ld_rows4(xblk + (c + 1) * 16, ld, nxt);  // next sub-chunk's old values, in flight meanwhile
+                tmem_wait16(accr);
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    acc[q] = __uint_as_float(accr[q]);
                 if (c + 1 == c_end) {  // this warp is done with the accumulator: tell the even CTA
                     tc_fence_before();
                     __syncwarp();
@@ -878,6 +905,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                         colred[(wq * NS + 0) * N2 + cc + lane] = t0;
                     }
                 }
+                if (c + 1 < c_end)
+                    tmem_ld16_nowait(tbase + cc + 16, accr);
                 // stage the new values (0 where nothing is stored) in this warp's block
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
