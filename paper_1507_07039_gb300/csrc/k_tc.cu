@@ -82,12 +82,17 @@ __device__ __forceinline__ float tanimoto_clamped(float num, float nx, float ny)
     return num * rsqrtf(fmaxf((nx + ny) - fabsf(num), 1e-30f));
 }
 
-// hi / lo of a whole array (padding stays zero because x is zero there)
+// hi / lo of a whole array (padding stays zero because x is zero there); L may be NULL (hi only)
 __global__ void k_split(const float *__restrict__ X, size_t n, __nv_bfloat16 *__restrict__ H,
                         __nv_bfloat16 *__restrict__ L)
 {
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
-        split_bf16(X[q], H[q], L[q]);
+    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(X[q], hi, lo);
+        H[q] = hi;
+        if (L)
+            L[q] = lo;
+    }
 }
 
 // hi / lo of two values at once, packed as BF16 pairs (first value in the low half)
@@ -425,26 +430,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                 if (!wait_bounded(&sy.empty[st], ((uint32_t)(kb / ST1) & 1u) ^ 1u, &sy.abort, ctl))
                     break;
                 const uint32_t fb = mapa_shared(smem_u32(&sy.full[st]), 0);
-                if (rank == 0)
-                    mbar_arrive_expect_tx(&sy.full[st], 2 * STAGE1);
+                if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half
+                    mbar_arrive_expect_tx(&sy.full[st], (d.split_b ? 8 : 6) * A_BYTES);
                 uint8_t *b = stages + (size_t)st * STAGE1;
                 if (kb < nR) {  // responsibility: P_off rows x W^T rows, K over TFs
                     const int k = kb * BK;
                     tma_load_2d_pair(b, &maps.Ph, fb, k, m0);
                     tma_load_2d_pair(b + A_BYTES, &maps.Pl, fb, k, m0);
                     tma_load_2d_pair(b + 2 * A_BYTES, &maps.Wth[cur], fb, k, nb0);
-                    tma_load_2d_pair(b + 3 * A_BYTES, &maps.Wtl[cur], fb, k, nb0);
+                    if (d.split_b)
+                        tma_load_2d_pair(b + 3 * A_BYTES, &maps.Wtl[cur], fb, k, nb0);
                 } else {        // availability: W rows x C_off rows, K over genes
                     const int k = (kb - nR) * BK;
                     tma_load_2d_pair(b, &maps.Wh[cur], fb, k, m0);
                     tma_load_2d_pair(b + A_BYTES, &maps.Wl[cur], fb, k, m0);
                     if (k >= n0) {  // C_off[j][k], k at or past the tile's diagonal block: stored rows
                         tma_load_2d_pair(b + 2 * A_BYTES, &maps.Ch, fb, k, nb0);
-                        tma_load_2d_pair(b + 3 * A_BYTES, &maps.Cl, fb, k, nb0);
+                        if (d.split_b)
+                            tma_load_2d_pair(b + 3 * A_BYTES, &maps.Cl, fb, k, nb0);
                     } else {        // k < j: C_off[j][k] = C_off[k][j], rows k of the upper triangle
                         for (int h = 0; h < 2; ++h) {
                             tma_load_2d_pair(b + 2 * A_BYTES + h * (A_BYTES / 2), &maps.Chm, fb, nb0 + 64 * h, k);
-                            tma_load_2d_pair(b + 3 * A_BYTES + h * (A_BYTES / 2), &maps.Clm, fb, nb0 + 64 * h, k);
+                            if (d.split_b)
+                                tma_load_2d_pair(b + 3 * A_BYTES + h * (A_BYTES / 2), &maps.Clm, fb, nb0 + 64 * h,
+                                                 k);
                         }
                     }
                 }
@@ -475,7 +484,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                     const uint64_t bl = bmn ? sdesc_mn_sw128(base + 3 * A_BYTES + kk * 2048, A_BYTES / 2)
                                             : sdesc_k_sw128(base + 3 * A_BYTES + off);
                     mma_bf16_pair(dacc, ah, bh, id, (fresh && kk == 0) ? 0u : 1u);
-                    mma_bf16_pair(dacc, ah, bl, id, 1u);
+                    if (d.split_b)
+                        mma_bf16_pair(dacc, ah, bl, id, 1u);
                     mma_bf16_pair(dacc, al, bh, id, 1u);
                 }
                 mma_commit_pair(&sy.empty[st]);
@@ -724,13 +734,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                         break;
                     }
                     const uint32_t fb = mapa_shared(smem_u32(&sy.full[st]), 0);
-                    if (rank == 0)
-                        mbar_arrive_expect_tx(&sy.full[st], 2 * STAGE2);
+                    if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half
+                        mbar_arrive_expect_tx(&sy.full[st], (d.split_b ? 8 : 6) * A_BYTES);
                     uint8_t *b = stages + (size_t)st * STAGE2;
                     tma_load_2d_pair(b, mh, fb, kb * BK, m0);
                     tma_load_2d_pair(b + A_BYTES, ml, fb, kb * BK, m0);
                     tma_load_2d_pair(b + 2 * A_BYTES, mh, fb, kb * BK, n0);
-                    tma_load_2d_pair(b + 3 * A_BYTES, ml, fb, kb * BK, n0);
+                    if (d.split_b)
+                        tma_load_2d_pair(b + 3 * A_BYTES, ml, fb, kb * BK, n0);
                 }
             }
             sy.issued = g;
@@ -764,7 +775,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                         const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
                         const uint64_t bl = sdesc_k_sw128(base + 3 * A_BYTES + off);
                         mma_bf16_pair(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
-                        mma_bf16_pair(dacc, ah, bl, idesc, 1u);
+                        if (d.split_b)
+                            mma_bf16_pair(dacc, ah, bl, idesc, 1u);
                         mma_bf16_pair(dacc, al, bh, idesc, 1u);
                     }
                     mma_commit_pair(&sy.empty[st]);
@@ -793,6 +805,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             const float *nrm = isP ? d.rsqW : d.csqW;
             float *X = isP ? d.Poff : d.Coff;
             __nv_bfloat16 *Xh = isP ? d.Ph : d.Ch, *Xl = isP ? d.Pl : d.Cl;
+            const bool wlo = isP || d.split_b;  // C's lo half is a B operand only: none under BF16X2
             // split copies of the lower triangle: all of P (phase 1 reads its rows K-major), but of C
             // only inside diagonal 256-blocks (phase 1 reads the rest of C's lower triangle MN-major)
             const bool mirror = isP || bm == bn;
@@ -927,14 +940,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                     if (kk < jj && jj + 3 < nn) {
                         *reinterpret_cast<float4 *>(X + ro) = make_float4(f[0], f[1], f[2], f[3]);
                         *reinterpret_cast<uint2 *>(Xh + ro) = make_uint2(h2[0], h2[1]);
-                        *reinterpret_cast<uint2 *>(Xl + ro) = make_uint2(l2[0], l2[1]);
+                        if (wlo)
+                            *reinterpret_cast<uint2 *>(Xl + ro) = make_uint2(l2[0], l2[1]);
                     } else {
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
                             if (kk < jj + q && jj + q < nn) {
                                 X[ro + q] = f[q];
                                 reinterpret_cast<uint16_t *>(Xh)[ro + q] = (uint16_t)(h2[q >> 1] >> (16 * (q & 1)));
-                                reinterpret_cast<uint16_t *>(Xl)[ro + q] = (uint16_t)(l2[q >> 1] >> (16 * (q & 1)));
+                                if (wlo)
+                                    reinterpret_cast<uint16_t *>(Xl)[ro + q] =
+                                        (uint16_t)(l2[q >> 1] >> (16 * (q & 1)));
                             }
                     }
                 }
@@ -973,7 +989,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                         if (mmask) {
                             const size_t mo = (size_t)jm * ld + km;
                             st16_packed(Xh + mo, hv, mmask);
-                            st16_packed(Xl + mo, lv, mmask);
+                            if (wlo)
+                                st16_packed(Xl + mo, lv, mmask);
                         }
                     }
                 }
@@ -1150,7 +1167,10 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s)
         k_split<<<1024, 256, 0, s>>>(d.Wt[b], TG, d.Wth[b], d.Wtl[b]);
     }
     k_split<<<1024, 256, 0, s>>>(d.Poff, (size_t)d.Tp * d.Tp, d.Ph, d.Pl);
-    k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, d.Cl);
+    if (d.split_b)
+        k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, d.Cl);
+    else
+        k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, nullptr);
     if ((e = cudaGetLastError()))
         return e;
     if (!d.tc_host) {
@@ -1159,8 +1179,10 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s)
         std::memset(m, 0, sizeof *m);
         d.tc_host = h;
         if ((e = make_map(&m->Ph, d.Ph, d.Tp, d.Tp, 128)) || (e = make_map(&m->Pl, d.Pl, d.Tp, d.Tp, 128)) ||
-            (e = make_map(&m->Ch, d.Ch, d.Gp, d.Gp, 128)) || (e = make_map(&m->Cl, d.Cl, d.Gp, d.Gp, 128)) ||
-            (e = make_map(&m->Chm, d.Ch, d.Gp, d.Gp, 64)) || (e = make_map(&m->Clm, d.Cl, d.Gp, d.Gp, 64)))
+            (e = make_map(&m->Ch, d.Ch, d.Gp, d.Gp, 128)) || (e = make_map(&m->Chm, d.Ch, d.Gp, d.Gp, 64)))
+            return e;
+        if (d.split_b &&
+            ((e = make_map(&m->Cl, d.Cl, d.Gp, d.Gp, 128)) || (e = make_map(&m->Clm, d.Cl, d.Gp, d.Gp, 64))))
             return e;
         for (int b = 0; b < 2; ++b)
             if ((e = make_map(&m->Wh[b], d.Wh[b], d.Tp, d.Gp, 128)) ||

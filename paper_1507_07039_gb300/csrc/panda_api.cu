@@ -42,6 +42,9 @@ namespace {
 
 thread_local std::string g_create_error = "no error";
 
+// the modes that run on the tensor-core path (k_tc.cu)
+bool tensor_prec(int prec) { return prec == PANDA_BF16X3 || prec == PANDA_BF16X2; }
+
 struct Fail {
     int code;
 };
@@ -110,6 +113,7 @@ int plan_memory(panda_ctx *c)
     const size_t Tp = c->Tp, Gp = c->Gp;
     d.T = c->T; d.G = c->G; d.Tp = c->Tp; d.Gp = c->Gp; d.nbT = c->nbT; d.nbG = c->nbG;
     d.diag = c->diag;
+    d.split_b = c->prec == PANDA_BF16X3 ? 1 : 0;
     for (int b = 0; b < 2; ++b) {
         DALLOC(d.W[b], Tp * Gp);
         DALLOC(d.Wt[b], Gp * Tp);
@@ -132,8 +136,8 @@ int plan_memory(panda_ctx *c)
     // partial-sum slots: one per 128-row block (FP32 path); on the tensor-core
     // path one per 256-column block for the row role plus one per 128-row half
     // for the column role (see k_tc.cu)
-    d.nsP = c->prec == PANDA_BF16X3 ? 3 * ceil_div(c->Tp, 256) : c->nbT;
-    d.nsC = c->prec == PANDA_BF16X3 ? 3 * ceil_div(c->Gp, 256) : c->nbG;
+    d.nsP = tensor_prec(c->prec) ? 3 * ceil_div(c->Tp, 256) : c->nbT;
+    d.nsC = tensor_prec(c->prec) ? 3 * ceil_div(c->Gp, 256) : c->nbG;
     DALLOC(d.ps_sum, (size_t)d.nsP * Tp);
     DALLOC(d.ps_sq, (size_t)d.nsP * Tp);
     DALLOC(d.ps_vsq, (size_t)d.nsP * Tp);
@@ -146,7 +150,7 @@ int plan_memory(panda_ctx *c)
     DALLOC(c->d_flags, 4);
     DALLOC(c->d_stats, 4);
     DALLOC(c->d_partials, 1024);
-    if (c->prec == PANDA_BF16X3) {
+    if (tensor_prec(c->prec)) {
         for (int b = 0; b < 2; ++b) {
             DALLOC(d.Wh[b], Tp * Gp);
             DALLOC(d.Wl[b], Tp * Gp);
@@ -156,7 +160,8 @@ int plan_memory(panda_ctx *c)
         DALLOC(d.Ph, Tp * Tp);
         DALLOC(d.Pl, Tp * Tp);
         DALLOC(d.Ch, Gp * Gp);
-        DALLOC(d.Cl, Gp * Gp);
+        if (d.split_b)
+            DALLOC(d.Cl, Gp * Gp);
     }
     return 0;
 }
@@ -242,7 +247,7 @@ int derive_state(panda_ctx *c, bool split_diag)
     CU(launch_col_norms(d.W[c->cur], c->T, c->G, c->Gp, d.csqW, c->stream));
     CU(launch_row_norms(d.Poff, c->T, c->T, c->Tp, d.pd, d.rsqP, c->stream));
     CU(launch_row_norms(d.Coff, c->G, c->G, c->Gp, d.cd, d.csqC, c->stream));
-    if (c->prec == PANDA_BF16X3)
+    if (tensor_prec(c->prec))
         CU(tc_prepare(d, c->stream));
     return 0;
 }
@@ -256,18 +261,18 @@ void drop_graphs(panda_ctx *c)
         }
 }
 
-int n_kernels(const panda_ctx *c) { return c->prec == PANDA_BF16X3 ? TC_KERNELS : SIMT_KERNELS; }
+int n_kernels(const panda_ctx *c) { return tensor_prec(c->prec) ? TC_KERNELS : SIMT_KERNELS; }
 
 const char *kernel_name(const panda_ctx *c, int i)
 {
-    return c->prec == PANDA_BF16X3 ? TC_KERNEL_NAMES[i] : SIMT_KERNEL_NAMES[i];
+    return tensor_prec(c->prec) ? TC_KERNEL_NAMES[i] : SIMT_KERNEL_NAMES[i];
 }
 
 // slot: which iteration of a graph (or chunk) this is, for the timing events
 int launch_iteration(panda_ctx *c, int cur, int slot)
 {
     KernelEvents ke{c->prof ? c->ev.data() + (size_t)slot * (n_kernels(c) + 1) : nullptr, 0};
-    cudaError_t e = c->prec == PANDA_BF16X3 ? launch_iteration_tc(c->d, cur, c->stream, ke)
+    cudaError_t e = tensor_prec(c->prec) ? launch_iteration_tc(c->d, cur, c->stream, ke)
                                             : launch_iteration_simt(c->d, cur, c->stream, ke);
     if (e != cudaSuccess)
         return set_err(c, PANDA_ECUDA, std::string("iteration launch: ") + cudaGetErrorString(e));
@@ -452,17 +457,17 @@ int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P
     panda_default_opts(&opts);
     if (o)
         opts = *o;
-    if (opts.prec != PANDA_FP32 && opts.prec != PANDA_BF16X3)
-        return set_err(nullptr, PANDA_EUNSUPPORTED, "precision mode not built (FP32 and BF16X3 are)");
+    if (opts.prec != PANDA_FP32 && !tensor_prec(opts.prec))
+        return set_err(nullptr, PANDA_EUNSUPPORTED, "precision mode not built (FP32, BF16X3 and BF16X2 are)");
     if (opts.diag < 0 || opts.diag > 2 || opts.t0 < 0 || opts.t0 >= HIST_CAP || opts.graph_iters < 0)
         return set_err(nullptr, PANDA_EINVAL, "bad option value");
-    if (opts.prec == PANDA_BF16X3 && !tc_supported())
-        return set_err(nullptr, PANDA_EUNSUPPORTED, "BF16X3 needs an sm_103 device");
+    if (tensor_prec(opts.prec) && !tc_supported())
+        return set_err(nullptr, PANDA_EUNSUPPORTED, "the tensor-core modes need an sm_103 device");
 
     panda_ctx *c = new panda_ctx();
     c->T = T; c->G = G;
     // the tensor-core path works on 256-row tiles of CTA pairs: pad to 256 there
-    const int granule = opts.prec == PANDA_BF16X3 ? 2 * TILE : TILE;
+    const int granule = tensor_prec(opts.prec) ? 2 * TILE : TILE;
     c->Tp = round_up(T, granule); c->Gp = round_up(G, granule);
     c->nbT = c->Tp / TILE; c->nbG = c->Gp / TILE;
     c->prec = opts.prec; c->diag = opts.diag; c->normalize = opts.normalize;
@@ -538,7 +543,7 @@ int panda_precision_supported(int prec)
         int n = 0;
         return cudaGetDeviceCount(&n) == cudaSuccess && n > 0;
     }
-    if (prec == PANDA_BF16X3)
+    if (tensor_prec(prec))
         return tc_supported() ? 1 : 0;
     return 0;
 }
@@ -603,7 +608,7 @@ int panda_run(panda_ctx *c, float alpha, double tol, int max_iter, int *iters_ou
 // The tensor-core path keeps only the upper triangle of FP32 P and C current.
 static int full_matrices(panda_ctx *c)
 {
-    if (c->prec == PANDA_BF16X3) {
+    if (tensor_prec(c->prec)) {
         CU(launch_symmetrize(c->d.Poff, c->T, c->Tp, c->stream));
         CU(launch_symmetrize(c->d.Coff, c->G, c->Gp, c->stream));
     }
@@ -768,7 +773,7 @@ int panda_load(panda_ctx *c, const void *buf, long long bytes)
     CU(launch_transpose(d.W[c->cur], c->Tp, c->Gp, d.Wt[c->cur], c->stream));
     CU(launch_diag_to_float(d.pd, d.pdf, c->T, c->stream));
     CU(launch_diag_to_float(d.cd, d.cdf, c->G, c->stream));
-    if (c->prec == PANDA_BF16X3)
+    if (tensor_prec(c->prec))
         CU(tc_prepare(d, c->stream));
     c->h_ctl->iters = h.iters;
     c->h_ctl->active = 0;

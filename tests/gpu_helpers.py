@@ -10,6 +10,14 @@ Tolerances (FP32 epilogues; derivation in the design notes):
     grow like e^{2 alpha t}.
   * iteration counts identical, unless the oracle's h lands within 1e-6 of tol
     at the stopping iteration, in which case both run the same fixed count.
+  * BF16X2 (B operands rounded to BF16, unit roundoff u = 2^-8): each product
+    misses sum_k hi(a_k) lo(b_k), of rms about u / sqrt(3) * sqrt(sum a^2 b^2);
+    after the Tanimoto division and the alpha / 2 damping that is about 1e-4 rms
+    per iteration in W at 1000 x 17000 (measured 1.1e-4), and the largest of
+    1e5 to 1e7 entries, compounded over a damped run, about 1e-3 (measured up to
+    1.4e-3).  Bound: 3e-3 for W and for the off-diagonal and diagonal errors.
+    This mode does not meet the 1e-4 gate on W; it is a speed / accuracy point.
+    Its runs are compared at the oracle's iteration count.
 """
 from __future__ import annotations
 
@@ -20,6 +28,7 @@ from paper_1507_07039_gb300 import synth
 TOL = {
     0: dict(W=1e-5, off=2e-5, diag=2e-5),  # PANDA_FP32
     1: dict(W=1e-4, off=2e-4, diag=2e-4),  # PANDA_BF16X3
+    2: dict(W=3e-3, off=3e-3, diag=3e-3),  # PANDA_BF16X2
 }
 
 
