@@ -53,7 +53,10 @@ typedef enum {
     PANDA_BF16X3 = 1, /* tensor cores: x = hi + lo in BF16, hi*hi + hi*lo + lo*hi, FP32 accumulation */
     PANDA_BF16X2 = 2, /* tensor cores: A operands split hi + lo, B operands BF16 hi only: hi*hi + lo*hi
                          (about 2^-9 relative error on each B entry; 2/3 of BF16X3's tensor work) */
-    PANDA_FP8MIX = 3  /* reserved: not built */
+    PANDA_FP8MIX = 3  /* tensor cores: W.C and W^T.W on E4M3 copies (one term, FP32 accumulation,
+                         one power-of-two scale per copy chosen from norm bounds so that no entry
+                         saturates); P.W and W.W^T as BF16X3.  About 2^-4 relative error per E4M3
+                         entry: W errors of order 1e-2 */
 } panda_prec;
 
 /* Reading of Eq. 6 (the paper prints no alpha on the diagonal increment). */
@@ -168,9 +171,10 @@ int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, do
  * lo*hi, terms = 1 uses hi*hi only; terms + 10 runs the same product on CTA
  * pairs (cta_group::2 MMAs over 256 x 256 tiles); terms + 20 does so with B
  * held transposed on the device ([K][N]) and fed to the MMAs MN-major, the
- * form the availability product reads the lower triangle of C in.
- * PANDA_EINVAL on other terms or non-positive sizes; PANDA_EUNSUPPORTED off
- * sm_103. */
+ * form the availability product reads the lower triangle of C in; terms = 8
+ * rounds A and B to E4M3 (nearest even, saturating) and sums their products
+ * on CTA pairs with kind::f8f6f4 MMAs (FP32 accumulation).  PANDA_EINVAL on
+ * other terms or non-positive sizes; PANDA_EUNSUPPORTED off sm_103. */
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms);
 
 /* Test of the bounded device waits (no paper counterpart): runs the

@@ -244,6 +244,19 @@ __device__ __forceinline__ void slot_sums(const float *const (&src)[NV], int nsl
     }
 }
 
+// The largest of one warp's values into *slot (float bits of non-negative
+// values order like the values, so an unsigned maximum is exact and the
+// result does not depend on the order of the warps).
+__device__ __forceinline__ void fp8_norm_max(unsigned *slot, float v)
+{
+    unsigned u = __float_as_uint(fmaxf(v, 0.0f));
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1)
+        u = max(u, __shfl_xor_sync(0xffffffffu, u, off));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(slot, u);
+}
+
 // rsqW[i] = sum_b wrow_part[b][i], csqW[j] = sum_b wcol_part[b][j] (FP64).
 // Blocks [0, ceil(T/32)) take rows of W, the rest its columns.
 __global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_reduce_wnorms(Dev d)
@@ -258,8 +271,12 @@ __global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_reduce_wnorms(Dev d)
     const float *const src[1] = {rows ? d.wrow_part : d.wcol_part};
     double out[1];
     slot_sums<1>(src, rows ? d.nbG : d.nbT, rows ? d.Tp : d.Gp, x, ok, out, sh);
-    if (ok && threadIdx.x < RS_ROWS)
+    if (threadIdx.x >= RS_ROWS)
+        return;
+    if (ok)
         (rows ? d.rsqW : d.csqW)[x] = (float)out[0];
+    if (d.fp8)
+        fp8_norm_max(&d.f8n[rows ? 2 : 3], ok ? (float)out[0] : 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -407,29 +424,34 @@ __global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_fin(Dev d)
     const float *const src[3] = {isP ? d.ps_sum : d.cs_sum, isP ? d.ps_sq : d.cs_sq, isP ? d.ps_vsq : d.cs_vsq};
     double sums[3];
     slot_sums<3>(src, nb, ld, i, ok, sums, sh);
-    if (!ok || threadIdx.x >= RS_ROWS)
+    if (threadIdx.x >= RS_ROWS)
         return;
-    const double s1 = sums[0], s2 = sums[1], sv = sums[2];
-    const double alpha = (double)ctl->alpha;
-    const int t = ctl->iters + 1;
-    const double growth = d.e2tab[t < HIST_CAP ? t : HIST_CAP];
-    double sigma = 0.0;  // population std of the n - 1 off-diagonal entries (0 for one entry)
-    if (n > 2) {
-        const double m = s1 / (double)(n - 1);
-        const double var = s2 / (double)(n - 1) - m * m;
-        sigma = var > 0.0 ? sqrt(var) : 0.0;
+    float nrm = 0.0f;  // the row's new squared norm (0 past the network)
+    if (ok) {
+        const double s1 = sums[0], s2 = sums[1], sv = sums[2];
+        const double alpha = (double)ctl->alpha;
+        const int t = ctl->iters + 1;
+        const double growth = d.e2tab[t < HIST_CAP ? t : HIST_CAP];
+        double sigma = 0.0;  // population std of the n - 1 off-diagonal entries (0 for one entry)
+        if (n > 2) {
+            const double m = s1 / (double)(n - 1);
+            const double var = s2 / (double)(n - 1) - m * m;
+            sigma = var > 0.0 ? sqrt(var) : 0.0;
+        }
+        const double gain = d.diag == 1 ? 1.0 : alpha;  // PANDA_DIAG_D0_LITERAL has no alpha
+        const double mult = isP ? (double)d.G : (double)d.T;  // N_a with P, N_e with C
+        double *dg = isP ? d.pd : d.cd;
+        const double nd = (1.0 - alpha) * dg[i] + gain * mult * sigma * growth;
+        dg[i] = nd;
+        const float ndf = (float)nd;
+        nrm = (float)(sv + nd * nd);
+        (isP ? d.pdf : d.cdf)[i] = ndf;
+        (isP ? d.rsqP : d.csqC)[i] = nrm;
+        if (!isfinite(ndf) || !isfinite(nrm))
+            atomicOr(&d.ctl->status, ST_NONFINITE);
     }
-    const double gain = d.diag == 1 ? 1.0 : alpha;  // PANDA_DIAG_D0_LITERAL has no alpha
-    const double mult = isP ? (double)d.G : (double)d.T;  // N_a with P, N_e with C
-    double *dg = isP ? d.pd : d.cd;
-    const double nd = (1.0 - alpha) * dg[i] + gain * mult * sigma * growth;
-    dg[i] = nd;
-    const float ndf = (float)nd;
-    const float nrm = (float)(sv + nd * nd);
-    (isP ? d.pdf : d.cdf)[i] = ndf;
-    (isP ? d.rsqP : d.csqC)[i] = nrm;
-    if (!isfinite(ndf) || !isfinite(nrm))
-        atomicOr(&d.ctl->status, ST_NONFINITE);
+    if (d.fp8)  // the whole first warp, past the network too
+        fp8_norm_max(&d.f8n[isP ? 0 : 1], nrm);
 }
 
 // h (Eq. 7), the counter and the stop test: one block.
@@ -458,6 +480,14 @@ __global__ void k_tail(Dev d)
         ctl->iters = t;
         ctl->h_last = h;
         ctl->converged = h < ctl->tol;
+        if (d.fp8) {  // the new state's norm maxima, and the scale of the next W' (Eq. 2)
+            for (int q = 0; q < 4; ++q) {
+                d.f8n[4 + q] = d.f8n[q];
+                d.f8n[q] = 0u;
+            }
+            d.f8[3] = e4m3_scale(fp8_bound_w(__uint_as_float(d.f8n[4]), __uint_as_float(d.f8n[5]),
+                                             __uint_as_float(d.f8n[6]), __uint_as_float(d.f8n[7])));
+        }
         if (!isfinite(h))
             ctl->status |= ST_NONFINITE;
         if (ctl->converged || t >= ctl->stop_at || ctl->status)

@@ -32,6 +32,8 @@
 #include <queue>
 #include <vector>
 
+#include <cuda_fp8.h>
+
 #include "panda_internal.cuh"
 #include "tc_common.cuh"
 
@@ -51,6 +53,7 @@ struct TcMaps {  // split copies, K-major, boxes of 64 x 128 (one CTA's half of 
     CUtensorMap Wth[2], Wtl[2];      // W^T split     [Gp][Tp]
     CUtensorMap Ch, Cl;              // C_off split   [Gp][Gp]
     CUtensorMap Chm, Clm;            // the same arrays in boxes of 64 x 64, for MN-major loads
+    CUtensorMap W8[2], Wt8[2], C8;   // FP8MIX: E4M3 copies, boxes of 128 B x 128 rows
 };
 
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
@@ -103,6 +106,59 @@ __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t &hi, uin
     const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
     hi = *reinterpret_cast<const uint32_t *>(&h);
     lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// x0, x1 scaled by s and rounded to E4M3 (nearest even, saturating to +-448), x0 in the low byte
+__device__ __forceinline__ uint32_t e4m3x2(float x0, float x1, float s)
+{
+    return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(x0 * s, x1 * s), __NV_SATFINITE, __NV_E4M3);
+}
+
+// E4M3 copy of a whole array, scaled by *scale (padding stays zero)
+__global__ void k_to_e4m3(const float *__restrict__ X, size_t n, uint8_t *__restrict__ Q, const float *scale)
+{
+    const float s = scale ? *scale : 1.0f;
+    for (size_t q = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x); q < n;
+         q += 2 * (size_t)gridDim.x * blockDim.x) {
+        const uint32_t v = e4m3x2(X[q], q + 1 < n ? X[q + 1] : 0.0f, s);
+        Q[q] = (uint8_t)v;
+        if (q + 1 < n)
+            Q[q + 1] = (uint8_t)(v >> 8);
+    }
+}
+
+// FP8MIX set-up (one block): the state's squared-norm maxima, latched; the
+// scales of the state's E4M3 copies (an entry is at most its row's norm) and
+// of the next W'.
+__global__ void k_fp8_init(Dev d)
+{
+    __shared__ float red[4][1024];
+    const float *v[4] = {d.rsqP, d.csqC, d.rsqW, d.csqW};
+    const int n[4] = {d.T, d.G, d.T, d.G};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float m = 0.0f;
+        for (int i = threadIdx.x; i < n[q]; i += blockDim.x)
+            m = fmaxf(m, v[q][i]);
+        red[q][threadIdx.x] = m;
+    }
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                red[q][threadIdx.x] = fmaxf(red[q][threadIdx.x], red[q][threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < 4; ++q) {
+            d.f8n[q] = 0u;
+            d.f8n[4 + q] = __float_as_uint(red[q][0]);
+        }
+        d.f8[0] = d.f8[1] = e4m3_scale(1.001f * sqrtf(red[2][0]));
+        d.f8[2] = e4m3_scale(1.001f * sqrtf(red[1][0]));
+        d.f8[3] = e4m3_scale(fp8_bound_w(red[0][0], red[1][0], red[2][0], red[3][0]));
+    }
 }
 
 __device__ __forceinline__ void ld16(const float *src, float (&v)[16])
@@ -243,14 +299,15 @@ struct SyncPair {
 };
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
-    k_tc_selftest_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl, int bmn)
+    k_tc_selftest_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl, int bmn, int fp8)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
     SyncPair &sy = *reinterpret_cast<SyncPair *>(stages + PAIR_ST * PAIR_STAGE);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
-    const int m0 = (blockIdx.x >> 1) * 256, n0 = blockIdx.y * PAIR_N, nk = Kp / BK;
+    // a k-block is 128 B of each row: 64 BF16 or 128 E4M3 values
+    const int m0 = (blockIdx.x >> 1) * 256, n0 = blockIdx.y * PAIR_N, nk = Kp / (fp8 ? 2 * BK : BK);
     if (threadIdx.x == 0) {
         for (int q = 0; q < PAIR_ST; ++q) {
             mbar_init(&sy.full[q], 1);
@@ -277,8 +334,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     break;
                 const uint32_t fb = mapa_shared(smem_u32(&sy.full[s]), 0);
                 if (rank == 0)
-                    mbar_arrive_expect_tx(&sy.full[s], 2 * PAIR_STAGE);
+                    mbar_arrive_expect_tx(&sy.full[s], fp8 ? 4 * A_BYTES : 2 * PAIR_STAGE);
                 uint8_t *st = stages + (size_t)s * PAIR_STAGE;
+                if (fp8) {  // E4M3: one A and one B tile of 128 rows x 128 B
+                    tma_load_2d_pair(st, &maps.Ah, fb, kb * 2 * BK, m0 + 128 * rank);
+                    tma_load_2d_pair(st + A_BYTES, &maps.Bh, fb, kb * 2 * BK, n0 + 128 * rank);
+                    continue;
+                }
                 tma_load_2d_pair(st, &maps.Ah, fb, kb * BK, m0 + 128 * rank);
                 tma_load_2d_pair(st + A_BYTES, &maps.Al, fb, kb * BK, m0 + 128 * rank);
                 if (bmn) {  // B^T stored [K][N]: two 64 x 64 boxes per CTA half, N contiguous
@@ -306,6 +368,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     break;
                 tc_fence_after();
                 const uint32_t base = smem_u32(stages + (size_t)s * PAIR_STAGE);
+                if (fp8) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)  // K = 32 per MMA, 32 B along the swizzled row
+                        mma_e4m3_pair(sy.tmem, sdesc_k_sw128(base + kk * 32), sdesc_k_sw128(base + A_BYTES + kk * 32),
+                                      idesc_e4m3_f32(256, PAIR_N), (kb == 0 && kk == 0) ? 0u : 1u);
+                    mma_commit_pair(&sy.empty[s]);
+                    continue;
+                }
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
                     const uint32_t off = kk * 32;
@@ -402,7 +472,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
     const int mt = blockIdx.x >> 1, nt = blockIdx.y;
     const int m0 = mt * 256 + 128 * (int)rank;  // this CTA's 128 rows (TFs)
     const int n0 = nt * 256;                    // the tile's 256 columns (genes)
-    const int nR = d.Tp / BK, nk = nR + d.Gp / BK;
+    // k-blocks: R-num over TFs (64 BF16 per row), then A-num over genes (64 BF16, or 128 E4M3 under FP8MIX)
+    const int nR = d.Tp / BK, nk = nR + d.Gp / (d.fp8 ? 2 * BK : BK);
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < ST1; ++q) {
@@ -430,8 +501,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                 if (!wait_bounded(&sy.empty[st], ((uint32_t)(kb / ST1) & 1u) ^ 1u, &sy.abort, ctl))
                     break;
                 const uint32_t fb = mapa_shared(smem_u32(&sy.full[st]), 0);
-                if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half
-                    mbar_arrive_expect_tx(&sy.full[st], (d.split_b ? 8 : 6) * A_BYTES);
+                if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half, 2 of E4M3
+                    mbar_arrive_expect_tx(&sy.full[st], (kb >= nR && d.fp8 ? 4 : (d.split_b ? 8 : 6)) * A_BYTES);
                 uint8_t *b = stages + (size_t)st * STAGE1;
                 if (kb < nR) {  // responsibility: P_off rows x W^T rows, K over TFs
                     const int k = kb * BK;
@@ -440,6 +511,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                     tma_load_2d_pair(b + 2 * A_BYTES, &maps.Wth[cur], fb, k, nb0);
                     if (d.split_b)
                         tma_load_2d_pair(b + 3 * A_BYTES, &maps.Wtl[cur], fb, k, nb0);
+                } else if (d.fp8) {  // availability on E4M3 copies (C8 holds both triangles)
+                    const int k = (kb - nR) * 2 * BK;
+                    tma_load_2d_pair(b, &maps.W8[cur], fb, k, m0);
+                    tma_load_2d_pair(b + A_BYTES, &maps.C8, fb, k, nb0);
                 } else {        // availability: W rows x C_off rows, K over genes
                     const int k = (kb - nR) * BK;
                     tma_load_2d_pair(b, &maps.Wh[cur], fb, k, m0);
@@ -472,6 +547,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                 const uint32_t base = smem_u32(stages + (size_t)st * STAGE1);
                 const uint32_t dacc = sy.tmem + (kb < nR ? 0u : 256u);
                 const bool fresh = kb == 0 || kb == nR;
+                if (kb >= nR && d.fp8) {
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk)  // K = 32 per MMA
+                        mma_e4m3_pair(dacc, sdesc_k_sw128(base + kk * 32), sdesc_k_sw128(base + A_BYTES + kk * 32),
+                                      idesc_e4m3_f32(256, 256), (fresh && kk == 0) ? 0u : 1u);
+                    mma_commit_pair(&sy.empty[st]);
+                    continue;
+                }
                 const bool bmn = kb >= nR && (kb - nR) * BK < n0;  // B block loaded MN-major
                 const uint32_t id = bmn ? (idesc | IDESC_B_MN) : idesc;
 #pragma unroll
@@ -502,6 +585,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
         const float *W = d.W[cur];
         float *Wn = d.W[nx];
         __nv_bfloat16 *Wh = d.Wh[nx], *Wl = d.Wl[nx], *Wth = d.Wth[nx], *Wtl = d.Wtl[nx];
+        // FP8MIX: the A-num accumulator holds the scaled E4M3 products; W' gets E4M3 copies too
+        const bool q8 = d.fp8 != 0;
+        const float ainv = q8 ? 1.0f / (d.f8[cur] * d.f8[2]) : 1.0f, s8 = q8 ? d.f8[3] : 1.0f;
+        if (q8 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 64)
+            d.f8[nx] = s8;  // the scale of W8[nx] and Wt8[nx] from here on
         // what does not depend on the accumulators is fetched before waiting for them
         {
             const int j = n0 + tt;
@@ -537,7 +625,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                 wn[q] = 0.0f;
                 if (ri && j0 + q < d.G) {
                     const float rnum = rr[q] + pdi * w[q];               // P_i. . W_.j
-                    const float anum = aa[q] + w[q] * colvec[cc + q];    // W_i. . C_.j
+                    const float anum = fmaf(aa[q], ainv, w[q] * colvec[cc + q]);  // W_i. . C_.j
                     const float R = tanimoto_fast(rnum, rsp, colvec[256 + cc + q]);
                     const float A = tanimoto_fast(anum, rsw, colvec[512 + cc + q]);
                     wn[q] = keep * w[q] + halfa * (A + R);
@@ -562,6 +650,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                 *reinterpret_cast<float4 *>(Wn + ro) = make_float4(f[0], f[1], f[2], f[3]);
                 *reinterpret_cast<uint2 *>(Wh + ro) = make_uint2(h2[0], h2[1]);
                 *reinterpret_cast<uint2 *>(Wl + ro) = make_uint2(l2[0], l2[1]);
+                if (q8)
+                    *reinterpret_cast<uint32_t *>(d.W8[nx] + ro) = e4m3x2(f[0], f[1], s8) | e4m3x2(f[2], f[3], s8) << 16;
             }
             // (b) the transposed split copies: lane l takes column (l & 15), rows 16 (l >> 4) + 0..15,
             //     and the column sums of W'^2 over the warp's 32 rows
@@ -585,6 +675,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
                 const size_t to = (size_t)(j0 + col) * d.Tp + k0 + h16;
                 st16_packed(Wth + to, hv, 0xffffu);
                 st16_packed(Wtl + to, lv, 0xffffu);
+                if (q8) {
+                    uint32_t p8[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        p8[q] = e4m3x2(g[4 * q], g[4 * q + 1], s8) | e4m3x2(g[4 * q + 2], g[4 * q + 3], s8) << 16;
+                    *reinterpret_cast<uint4 *>(d.Wt8[nx] + to) = make_uint4(p8[0], p8[1], p8[2], p8[3]);
+                }
             }
             __syncwarp();
         }
@@ -724,7 +821,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                 const int tile = sched[n];
                 const bool isP = tile < 0;
                 const int m0 = ((tile >> 16) & 0x7fff) * N2 + 128 * rank, n0 = (tile & 0xffff) * N2 + 128 * rank;
-                const int nk = (isP ? d.Gp : d.Tp) / BK;
+                const bool q8 = d.fp8 && !isP;  // FP8MIX: C tiles from the E4M3 copy of W'^T, one term
+                const int nk = isP ? d.Gp / BK : d.Tp / (q8 ? 2 * BK : BK);
                 const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Wth[cur];
                 const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl[cur];
                 for (int kb = 0; kb < nk; ++kb, ++g) {
@@ -734,9 +832,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                         break;
                     }
                     const uint32_t fb = mapa_shared(smem_u32(&sy.full[st]), 0);
-                    if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half
-                        mbar_arrive_expect_tx(&sy.full[st], (d.split_b ? 8 : 6) * A_BYTES);
+                    if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half, 2 of E4M3
+                        mbar_arrive_expect_tx(&sy.full[st], (q8 ? 4 : (d.split_b ? 8 : 6)) * A_BYTES);
                     uint8_t *b = stages + (size_t)st * STAGE2;
+                    if (q8) {
+                        tma_load_2d_pair(b, &maps.Wt8[cur], fb, kb * 2 * BK, m0);
+                        tma_load_2d_pair(b + A_BYTES, &maps.Wt8[cur], fb, kb * 2 * BK, n0);
+                        continue;
+                    }
                     tma_load_2d_pair(b, mh, fb, kb * BK, m0);
                     tma_load_2d_pair(b + A_BYTES, ml, fb, kb * BK, m0);
                     tma_load_2d_pair(b + 2 * A_BYTES, mh, fb, kb * BK, n0);
@@ -753,7 +856,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             bool ok = true;
             for (int n = first, idx = 0; n < last && ok; ++n, ++idx) {
                 const int tile = sched[n];
-                const int nk = (tile < 0 ? d.Gp : d.Tp) / BK;
+                const bool q8 = d.fp8 && tile >= 0;
+                const int nk = tile < 0 ? d.Gp / BK : d.Tp / (q8 ? 2 * BK : BK);
                 const int buf = idx & 1;
                 if (!wait_bounded(&sy.tempty[buf], ((uint32_t)(idx >> 1) & 1u) ^ 1u, &sy.abort, ctl))
                     break;
@@ -767,6 +871,15 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                     }
                     tc_fence_after();
                     const uint32_t base = smem_u32(stages + (size_t)st * STAGE2);
+                    if (q8) {
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)  // K = 32 per MMA
+                            mma_e4m3_pair(dacc, sdesc_k_sw128(base + kk * 32),
+                                          sdesc_k_sw128(base + A_BYTES + kk * 32), idesc_e4m3_f32(256, N2),
+                                          (kb == 0 && kk == 0) ? 0u : 1u);
+                        mma_commit_pair(&sy.empty[st]);
+                        continue;
+                    }
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
                         const uint32_t off = kk * 32;
@@ -795,6 +908,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
         const int tt = threadIdx.x - 64;  // 0..383
         const float a = ctl->alpha, keep = 1.0f - a;
         const uint32_t tempty_even = mapa_shared(smem_u32(&sy.tempty[0]), 0);
+        // FP8MIX: C-tile accumulators hold products of W'^T scaled by f8[cur] on both sides; C' gets
+        // an E4M3 copy scaled so that no entry saturates (bound from |C_k.| and |W'_.k|)
+        const float sw = d.fp8 ? d.f8[cur] : 1.0f, ainv2 = 1.0f / (sw * sw);
+        const float sC = d.fp8 ? e4m3_scale(fp8_bound_c(__uint_as_float(d.f8n[5]), __uint_as_float(d.f8n[3])))
+                               : 1.0f;
+        if (d.fp8 && blockIdx.x == 0 && threadIdx.x == 64)
+            d.f8[2] = sC;  // the scale of C8 from here on
         for (int n = first, idx = 0; n < last; ++n, ++idx) {
             const int tile = sched[n];
             const bool isP = tile < 0;
@@ -808,7 +928,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             const bool wlo = isP || d.split_b;  // C's lo half is a B operand only: none under BF16X2
             // split copies of the lower triangle: all of P (phase 1 reads its rows K-major), but of C
             // only inside diagonal 256-blocks (phase 1 reads the rest of C's lower triangle MN-major)
-            const bool mirror = isP || bm == bn;
+            const bool q8 = d.fp8 && !isP;
+            const bool mirror = isP || bm == bn || q8;  // the E4M3 copy of C holds both triangles
+            const float ascale = q8 ? ainv2 : 1.0f;
             const int buf = idx & 1;
             // everything that does not depend on the accumulator is fetched before waiting for it:
             // the tile's column norms (shared), this row's norm and its first old values
@@ -857,7 +979,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                 tmem_wait16(accr);
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    acc[q] = __uint_as_float(accr[q]);
+                    acc[q] = __uint_as_float(accr[q]) * ascale;
                 if (c + 1 == c_end) {  // this warp is done with the accumulator: tell the even CTA
                     tc_fence_before();
                     __syncwarp();
@@ -933,10 +1055,25 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
                         f[q] = blk[rr * 17 + 4 * (lane & 3) + q];
+                    const size_t ro = (size_t)kk * ld + jj;
+                    if (q8) {
+                        if (kk < jj && jj + 3 < nn) {
+                            *reinterpret_cast<float4 *>(X + ro) = make_float4(f[0], f[1], f[2], f[3]);
+                            *reinterpret_cast<uint32_t *>(d.C8 + ro) =
+                                e4m3x2(f[0], f[1], sC) | e4m3x2(f[2], f[3], sC) << 16;
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (kk < jj + q && jj + q < nn) {
+                                    X[ro + q] = f[q];
+                                    d.C8[ro + q] = (uint8_t)e4m3x2(f[q], 0.0f, sC);
+                                }
+                        }
+                        continue;
+                    }
                     uint32_t h2[2], l2[2];
                     split_pair(f[0], f[1], h2[0], l2[0]);
                     split_pair(f[2], f[3], h2[1], l2[1]);
-                    const size_t ro = (size_t)kk * ld + jj;
                     if (kk < jj && jj + 3 < nn) {
                         *reinterpret_cast<float4 *>(X + ro) = make_float4(f[0], f[1], f[2], f[3]);
                         *reinterpret_cast<uint2 *>(Xh + ro) = make_uint2(h2[0], h2[1]);
@@ -978,7 +1115,26 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                             colred[(wq * NS + 1) * N2 + cc + lane] = c2;
                         }
                     }
-                    if (mirror) {
+                    if (mirror && q8) {
+                        const int jm = j0 + col, km = k0 + h16;
+                        const uint32_t mmask =
+                            jm >= nn ? 0u : (km + 15 < jm ? 0xffffu : (km >= jm ? 0u : ((1u << (jm - km)) - 1u)));
+                        if (mmask) {
+                            uint32_t p8[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                p8[q] = e4m3x2(g[4 * q], g[4 * q + 1], sC) | e4m3x2(g[4 * q + 2], g[4 * q + 3], sC) << 16;
+                            uint8_t *dst = d.C8 + (size_t)jm * ld + km;
+                            if (mmask == 0xffffu) {
+                                *reinterpret_cast<uint4 *>(dst) = make_uint4(p8[0], p8[1], p8[2], p8[3]);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 16; ++q)
+                                    if (mmask >> q & 1u)
+                                        dst[q] = (uint8_t)(p8[q >> 2] >> (8 * (q & 3)));
+                            }
+                        }
+                    } else if (mirror) {
                         uint32_t hv[8], lv[8];
 #pragma unroll
                         for (int q = 0; q < 8; ++q)
@@ -1072,6 +1228,22 @@ cudaError_t make_map(CUtensorMap *m, const void *base, int rows, int cols, int b
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// 8-bit [rows][cols] array (E4M3 bytes), boxes of 128 bytes by box_rows rows
+cudaError_t make_map8(CUtensorMap *m, const void *base, int rows, int cols, int box_rows)
+{
+    auto fn = encode_fn();
+    if (!fn)
+        return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols};
+    cuuint32_t box[2] = {128, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 constexpr size_t pair_smem() { return 1024 + (size_t)PAIR_ST * PAIR_STAGE + sizeof(SyncPair) + 16; }
 
 struct TcHost {
@@ -1155,7 +1327,7 @@ bool tc_supported()
     return major == 10 && minor == 3 && encode_fn() != nullptr;
 }
 
-cudaError_t tc_prepare(Dev &d, cudaStream_t s)
+cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales)
 {
     cudaError_t e = set_smem_limits();
     if (e)
@@ -1167,10 +1339,19 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s)
         k_split<<<1024, 256, 0, s>>>(d.Wt[b], TG, d.Wth[b], d.Wtl[b]);
     }
     k_split<<<1024, 256, 0, s>>>(d.Poff, (size_t)d.Tp * d.Tp, d.Ph, d.Pl);
-    if (d.split_b)
+    if (d.fp8) {  // scales from the state's norms (or as restored), then the E4M3 copies
+        if (fresh_scales)
+            k_fp8_init<<<1, 1024, 0, s>>>(d);
+        for (int b = 0; b < 2; ++b) {
+            k_to_e4m3<<<1024, 256, 0, s>>>(d.W[b], TG, d.W8[b], d.f8 + b);
+            k_to_e4m3<<<1024, 256, 0, s>>>(d.Wt[b], TG, d.Wt8[b], d.f8 + b);
+        }
+        k_to_e4m3<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.C8, d.f8 + 2);
+    } else if (d.split_b) {
         k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, d.Cl);
-    else
+    } else {
         k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, nullptr);
+    }
     if ((e = cudaGetLastError()))
         return e;
     if (!d.tc_host) {
@@ -1178,12 +1359,22 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s)
         TcMaps *m = &h->maps;
         std::memset(m, 0, sizeof *m);
         d.tc_host = h;
-        if ((e = make_map(&m->Ph, d.Ph, d.Tp, d.Tp, 128)) || (e = make_map(&m->Pl, d.Pl, d.Tp, d.Tp, 128)) ||
-            (e = make_map(&m->Ch, d.Ch, d.Gp, d.Gp, 128)) || (e = make_map(&m->Chm, d.Ch, d.Gp, d.Gp, 64)))
+        if ((e = make_map(&m->Ph, d.Ph, d.Tp, d.Tp, 128)) || (e = make_map(&m->Pl, d.Pl, d.Tp, d.Tp, 128)))
             return e;
-        if (d.split_b &&
-            ((e = make_map(&m->Cl, d.Cl, d.Gp, d.Gp, 128)) || (e = make_map(&m->Clm, d.Cl, d.Gp, d.Gp, 64))))
-            return e;
+        if (d.fp8) {
+            if ((e = make_map8(&m->C8, d.C8, d.Gp, d.Gp, 128)))
+                return e;
+            for (int b = 0; b < 2; ++b)
+                if ((e = make_map8(&m->W8[b], d.W8[b], d.Tp, d.Gp, 128)) ||
+                    (e = make_map8(&m->Wt8[b], d.Wt8[b], d.Gp, d.Tp, 128)))
+                    return e;
+        } else {
+            if ((e = make_map(&m->Ch, d.Ch, d.Gp, d.Gp, 128)) || (e = make_map(&m->Chm, d.Ch, d.Gp, d.Gp, 64)))
+                return e;
+            if (d.split_b &&
+                ((e = make_map(&m->Cl, d.Cl, d.Gp, d.Gp, 128)) || (e = make_map(&m->Clm, d.Cl, d.Gp, d.Gp, 64))))
+                return e;
+        }
         for (int b = 0; b < 2; ++b)
             if ((e = make_map(&m->Wh[b], d.Wh[b], d.Tp, d.Gp, 128)) ||
                 (e = make_map(&m->Wl[b], d.Wl[b], d.Tp, d.Gp, 128)) ||
@@ -1243,7 +1434,10 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     cudaError_t e = set_smem_limits();
     if (e)
         return e;
-    const int Mp = round_up(M, pair ? 256 : 128), Np = round_up(N, pair ? PAIR_N : 128), Kp = round_up(K, 64);
+    // pair: 0 one CTA per tile, 1 CTA pairs, 2 pairs with B MN-major, 3 pairs on E4M3 operands (one term)
+    const bool fp8 = pair == 3;
+    const int Mp = round_up(M, pair ? 256 : 128), Np = round_up(N, pair ? PAIR_N : 128),
+              Kp = round_up(K, fp8 ? 128 : 64);
     float *dA = nullptr, *dB = nullptr, *dD = nullptr;
     __nv_bfloat16 *Ah = nullptr, *Al = nullptr, *Bh = nullptr, *Bl = nullptr;
     Ctl *ctl = nullptr;
@@ -1278,6 +1472,22 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     } else {
         TRY(cudaMemcpy2D(dB, (size_t)Kp * 4, B, (size_t)K * 4, (size_t)K * 4, N, cudaMemcpyHostToDevice));
     }
+    if (fp8) {  // E4M3 bytes in the hi buffers (each at least as large as an 8-bit copy)
+        k_to_e4m3<<<256, 256>>>(dA, (size_t)Mp * Kp, reinterpret_cast<uint8_t *>(Ah), nullptr);
+        k_to_e4m3<<<256, 256>>>(dB, (size_t)Np * Kp, reinterpret_cast<uint8_t *>(Bh), nullptr);
+        TRY(cudaGetLastError());
+        TRY(make_map8(&maps.Ah, Ah, Mp, Kp, 128));
+        TRY(make_map8(&maps.Bh, Bh, Np, Kp, 128));
+        k_tc_selftest_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl, 0, 1);
+        TRY(cudaGetLastError());
+        TRY(cudaDeviceSynchronize());
+        Ctl h;
+        TRY(cudaMemcpy(&h, ctl, sizeof h, cudaMemcpyDeviceToHost));
+        *status = h.status;
+        TRY(cudaMemcpy2D(D, (size_t)N * 4, dD, (size_t)Np * 4, (size_t)N * 4, M, cudaMemcpyDeviceToHost));
+        cleanup();
+        return cudaSuccess;
+    }
     k_split<<<256, 256>>>(dA, (size_t)Mp * Kp, Ah, Al);
     k_split<<<256, 256>>>(dB, (size_t)Np * Kp, Bh, Bl);
     TRY(cudaGetLastError());
@@ -1297,7 +1507,7 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
     if (pair)
         k_tc_selftest_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl,
-                                                                                    pair == 2);
+                                                                                    pair == 2, 0);
     else
         k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl, stall_kb);
     TRY(cudaGetLastError());

@@ -43,7 +43,7 @@ namespace {
 thread_local std::string g_create_error = "no error";
 
 // the modes that run on the tensor-core path (k_tc.cu)
-bool tensor_prec(int prec) { return prec == PANDA_BF16X3 || prec == PANDA_BF16X2; }
+bool tensor_prec(int prec) { return prec == PANDA_BF16X3 || prec == PANDA_BF16X2 || prec == PANDA_FP8MIX; }
 
 struct Fail {
     int code;
@@ -113,7 +113,8 @@ int plan_memory(panda_ctx *c)
     const size_t Tp = c->Tp, Gp = c->Gp;
     d.T = c->T; d.G = c->G; d.Tp = c->Tp; d.Gp = c->Gp; d.nbT = c->nbT; d.nbG = c->nbG;
     d.diag = c->diag;
-    d.split_b = c->prec == PANDA_BF16X3 ? 1 : 0;
+    d.split_b = c->prec == PANDA_BF16X2 ? 0 : 1;  // the BF16 products of FP8MIX are BF16X3
+    d.fp8 = c->prec == PANDA_FP8MIX ? 1 : 0;
     for (int b = 0; b < 2; ++b) {
         DALLOC(d.W[b], Tp * Gp);
         DALLOC(d.Wt[b], Gp * Tp);
@@ -159,9 +160,19 @@ int plan_memory(panda_ctx *c)
         }
         DALLOC(d.Ph, Tp * Tp);
         DALLOC(d.Pl, Tp * Tp);
-        DALLOC(d.Ch, Gp * Gp);
-        if (d.split_b)
-            DALLOC(d.Cl, Gp * Gp);
+        if (d.fp8) {  // W.C and W^T.W on E4M3 copies; no BF16 copy of C
+            for (int b = 0; b < 2; ++b) {
+                DALLOC(d.W8[b], Tp * Gp);
+                DALLOC(d.Wt8[b], Gp * Tp);
+            }
+            DALLOC(d.C8, Gp * Gp);
+            DALLOC(d.f8, 4);
+            DALLOC(d.f8n, 8);
+        } else {
+            DALLOC(d.Ch, Gp * Gp);
+            if (d.split_b)
+                DALLOC(d.Cl, Gp * Gp);
+        }
     }
     return 0;
 }
@@ -458,7 +469,7 @@ int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P
     if (o)
         opts = *o;
     if (opts.prec != PANDA_FP32 && !tensor_prec(opts.prec))
-        return set_err(nullptr, PANDA_EUNSUPPORTED, "precision mode not built (FP32, BF16X3 and BF16X2 are)");
+        return set_err(nullptr, PANDA_EUNSUPPORTED, "unknown precision mode");
     if (opts.diag < 0 || opts.diag > 2 || opts.t0 < 0 || opts.t0 >= HIST_CAP || opts.graph_iters < 0)
         return set_err(nullptr, PANDA_EINVAL, "bad option value");
     if (tensor_prec(opts.prec) && !tc_supported())
@@ -713,9 +724,14 @@ std::vector<CkptItem> ckpt_items(panda_ctx *c)
 {
     Dev &d = c->d;
     const size_t Tp = c->Tp, Gp = c->Gp;
-    return {{d.W[c->cur], Tp * Gp * 4}, {d.Poff, Tp * Tp * 4}, {d.Coff, Gp * Gp * 4},
-            {d.pd, Tp * 8},   {d.cd, Gp * 8},   {d.rsqP, Tp * 4}, {d.csqC, Gp * 4},
-            {d.rsqW, Tp * 4}, {d.csqW, Gp * 4}, {d.hist, (size_t)HIST_CAP * 8}};
+    std::vector<CkptItem> v = {{d.W[c->cur], Tp * Gp * 4}, {d.Poff, Tp * Tp * 4}, {d.Coff, Gp * Gp * 4},
+                               {d.pd, Tp * 8},   {d.cd, Gp * 8},   {d.rsqP, Tp * 4}, {d.csqC, Gp * 4},
+                               {d.rsqW, Tp * 4}, {d.csqW, Gp * 4}, {d.hist, (size_t)HIST_CAP * 8}};
+    if (d.fp8) {  // the E4M3 scales and latched norm maxima, so that a resumed run continues bit for bit
+        v.push_back({d.f8, 4 * sizeof(float)});
+        v.push_back({d.f8n, 8 * sizeof(unsigned)});
+    }
+    return v;
 }
 }  // namespace
 
@@ -774,7 +790,7 @@ int panda_load(panda_ctx *c, const void *buf, long long bytes)
     CU(launch_diag_to_float(d.pd, d.pdf, c->T, c->stream));
     CU(launch_diag_to_float(d.cd, d.cdf, c->G, c->stream));
     if (tensor_prec(c->prec))
-        CU(tc_prepare(d, c->stream));
+        CU(tc_prepare(d, c->stream, false));  // keep the saved E4M3 scales
     c->h_ctl->iters = h.iters;
     c->h_ctl->active = 0;
     c->h_ctl->status = 0;
@@ -849,10 +865,15 @@ int panda_selftest_timeout(void)
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms)
 {
     // terms + 10: the same product on CTA pairs (cta_group::2, 256 x 256 tiles);
-    // terms + 20: on CTA pairs with B stored transposed and loaded MN-major
-    const int pair = terms / 10;
+    // terms + 20: on CTA pairs with B stored transposed and loaded MN-major;
+    // terms = 8: E4M3 operands, one term, on CTA pairs
+    int pair = terms / 10;
     terms %= 10;
-    if (pair > 2)
+    if (terms == 8 && pair == 0) {
+        pair = 3;
+        terms = 1;
+    }
+    if (pair > 3)
         return set_err(nullptr, PANDA_EINVAL, "panda_selftest_tc_gemm: bad argument");
     if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !D || (terms != 1 && terms != 3))
         return set_err(nullptr, PANDA_EINVAL, "panda_selftest_tc_gemm: bad argument");

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cmath>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -63,8 +64,43 @@ struct Dev {
     // 1: B operands carry their lo halves too (BF16X3, hi.hi + hi.lo + lo.hi);
     // 0: B operands are BF16 hi only (BF16X2, hi.hi + lo.hi; C's lo half is never made)
     int split_b;
+    // FP8MIX: E4M3 copies (one byte per entry) for W.C and W^T.W, and their scales
+    int fp8;
+    uint8_t *W8[2], *Wt8[2];     // W [Tp][Gp] and W^T [Gp][Tp], entries times f8[b]
+    uint8_t *C8;                 // C_off [Gp][Gp], both triangles, entries times f8[2]
+    float *f8;                   // [0], [1]: scale of W8/Wt8 buffer b; [2]: of C8; [3]: for the next W'
+    unsigned *f8n;               // squared-norm maxima (float bits): [0..3] this iteration's
+                                 // (rsqP, csqC, rsqW, csqW), [4..7] the state's, latched
     void *tc_host;               // host-side tensor maps of the split copies (tensor-core path)
 };
+
+// Largest power of two s with s * bound <= 448 (the largest finite E4M3 value):
+// bound >= every |x| that is scaled by s, so no entry saturates.
+__host__ __device__ inline float e4m3_scale(float bound)
+{
+    if (!(bound > 0.0f) || !(bound < 3.0e38f))
+        return 1.0f;
+    const float x = 448.0f / bound;
+    union { float f; unsigned u; } v{x};
+    int e = (int)((v.u >> 23) & 0xffu) - 127;  // floor(log2 x) for normal x
+    e = e < -100 ? -100 : (e > 100 ? 100 : e);
+    v.u = (unsigned)(e + 127) << 23;
+    return v.f;
+}
+
+// The alpha-free bounds behind the scales.  |Tan(x, y)| <= sqrt(|x| |y|) (Eq. 1);
+// the damped updates are convex combinations, so |W'| <= max(|W|, (|R| + |A|) / 2)
+// and |C'| <= max(|C|, |Tan|).  An entry is at most its row's norm.  The factor
+// 1.25 covers E4M3 numerators, which may exceed the exact products by ~2^-4 per term.
+__host__ __device__ inline float fp8_bound_w(float mrP, float mcC, float mrW, float mcW)
+{
+    const float t = 1.25f * 0.5f * (sqrtf(sqrtf(mrP) * sqrtf(mcW)) + sqrtf(sqrtf(mrW) * sqrtf(mcC)));
+    return 1.001f * fmaxf(sqrtf(mrW), t);
+}
+__host__ __device__ inline float fp8_bound_c(float mcC, float mcW)
+{
+    return 1.001f * fmaxf(sqrtf(mcC), 1.25f * sqrtf(mcW));
+}
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ inline int round_up(int a, int b) { return ceil_div(a, b) * b; }
@@ -118,7 +154,8 @@ cudaError_t launch_reduce_wnorms(const Dev &d, cudaStream_t s);
 constexpr int TC_KERNELS = 5;
 extern const char *const TC_KERNEL_NAMES[TC_KERNELS];
 bool tc_supported();
-cudaError_t tc_prepare(Dev &d, cudaStream_t s);  // split copies of the state, tensor maps
+// fresh_scales: derive the FP8MIX scales from the state's norms (false: keep those restored)
+cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales = true);  // split copies of the state, tensor maps
 void tc_release(Dev &d);
 cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
 // D (M x N, row-major) = A (M x K) . B (N x K)^T through the tcgen05 pipeline,

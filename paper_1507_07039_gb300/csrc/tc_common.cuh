@@ -271,6 +271,26 @@ __device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t a_desc, 
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+// Instruction descriptor of kind::f8f6f4 with E4M3 A and B (format 0 in bits
+// 7-9 and 10-12), FP32 accumulator (bits 4-5 = 1), both operands K-major.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N)
+{
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// One pair MMA on 8-bit operands: K = 32 per instruction (32 bytes of each
+// 128-byte swizzled row, the same byte step as a BF16 MMA's K = 16).
+__device__ __forceinline__ void mma_e4m3_pair(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                              uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive on the barrier at this shared offset in both CTAs of the pair once
 // the pair's MMAs issued so far are done.
 __device__ __forceinline__ void mma_commit_pair(uint64_t *bar)

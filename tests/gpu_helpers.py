@@ -18,6 +18,13 @@ Tolerances (FP32 epilogues; derivation in the design notes):
     1.4e-3).  Bound: 3e-3 for W and for the off-diagonal and diagonal errors.
     This mode does not meet the 1e-4 gate on W; it is a speed / accuracy point.
     Its runs are compared at the oracle's iteration count.
+  * FP8MIX (W.C and W^T.W on E4M3 copies: unit roundoff 2^-4 on both operands,
+    16 x sqrt(2) times the BF16X2 per-product error): about 2e-3 rms per
+    iteration in W at 1000 x 17000 (measured 1.5e-3 rms, 8.4e-3 max after one
+    iteration); over the parity cases the worst error is 4.2e-2 (W) and 4.0e-2
+    (a diagonal).  Bound: 1e-1 for W, off-diagonal and diagonal, which any
+    wrong scale (a factor of 2 at least) or a missing term exceeds.  Compared
+    at the oracle's iteration count.
 """
 from __future__ import annotations
 
@@ -29,6 +36,7 @@ TOL = {
     0: dict(W=1e-5, off=2e-5, diag=2e-5),  # PANDA_FP32
     1: dict(W=1e-4, off=2e-4, diag=2e-4),  # PANDA_BF16X3
     2: dict(W=3e-3, off=3e-3, diag=3e-3),  # PANDA_BF16X2
+    3: dict(W=1e-1, off=1e-1, diag=1e-1),  # PANDA_FP8MIX
 }
 
 

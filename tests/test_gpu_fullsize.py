@@ -13,7 +13,7 @@ from oracle.oracle import Oracle
 
 pytestmark = pytest.mark.gpu
 
-PRECS = [0, 1, 2]  # PANDA_FP32, PANDA_BF16X3, PANDA_BF16X2
+PRECS = [0, 1, 2, 3]  # PANDA_FP32, PANDA_BF16X3, PANDA_BF16X2, PANDA_FP8MIX
 
 
 @pytest.fixture(scope="module")

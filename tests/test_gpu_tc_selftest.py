@@ -89,6 +89,31 @@ def test_cta_pair_product_mn_major_b(M, N, K):
     assert np.max(np.abs(D3 - panda.panda_selftest_tc_gemm(A, B, terms=13))) / scale < 1e-5
 
 
+def e4m3(x: np.ndarray) -> np.ndarray:
+    """x rounded to E4M3 (nearest even), as float64 (|x| stays below 448 here)."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+    return t.to(torch.float8_e4m3fn).to(torch.float32).double().numpy()
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 256, 128), (300, 600, 1000), (512, 256, 130)])
+def test_cta_pair_e4m3_product(M, N, K):
+    """kind::f8f6f4 MMAs on CTA pairs: products of E4M3 values are exact in
+    FP32, so only the FP32 accumulation separates D from the FP64 product of
+    the rounded operands."""
+    from paper_1507_07039_gb300 import panda
+    rng = np.random.default_rng(11 * M + N + K)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    D = panda.panda_selftest_tc_gemm(A, B, terms=8)
+    ref = e4m3(A) @ e4m3(B).T
+    scale = max(1.0, np.max(np.abs(ref)))
+    assert np.max(np.abs(D - ref)) / scale < 1e-5
+    # and E4M3 keeps about 2^-4 of each operand: far from the exact product, as it should be
+    exact = A.astype(np.float64) @ B.astype(np.float64).T
+    assert np.max(np.abs(D - exact)) / scale > 1e-4
+
+
 def test_bounded_wait_reports_timeout_and_device_stays_usable():
     """A pipeline stage armed but never loaded: the kernel's bounded waits
     must end it with PANDA_ETIMEOUT (about a second), not hang; the next
