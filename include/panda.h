@@ -198,11 +198,18 @@ void panda_destroy(panda_ctx *ctx);
 /* ---- sets of networks ----------------------------------------------------------
  * The paper's applications compare sets of networks, one per condition or
  * sample (Section I).  A batch holds n independent networks of their own
- * sizes, each a context of its own (own device state and stream), created
- * with the same options.  panda_batch_run iterates all of them at once: every
- * network still running queues its next chunk of iterations (a captured CUDA
- * graph) on its own stream, so small networks overlap on the GPU, and each one
- * stops on its own h < tol (or max_iter). */
+ * sizes, each a context of its own (own device state), created with the same
+ * options; each stops on its own h < tol (or max_iter).
+ * Tensor-core modes: panda_batch_run iterates all of them together with one
+ * launch per phase over every network's tiles (phase 1 over all their W'
+ * tiles, phase 2 persistent over one longest-first schedule of all their P and
+ * C tiles, then the norm and stop kernels over all their rows), a chunk of
+ * iterations captured as one CUDA graph.  The phase-2 schedule is autotuned:
+ * the first iterations a batch runs try schedules built for several epilogue
+ * weights, one iteration each, and the fastest is kept.  A tile's result does
+ * not depend on the schedule, so every network's results equal, bit for bit,
+ * those of the same network run alone.
+ * FP32: every network queues its chunks (a CUDA graph each) on its own stream. */
 typedef struct panda_batch panda_batch;
 
 /* T[k], G[k], W0[k], P0[k], C0[k] as in panda_create for network k (host
@@ -224,6 +231,14 @@ int panda_batch_get(panda_batch *b, int k, float *W, float *P, float *C);
  * destroy it; it accepts the per-context calls such as panda_get_history). */
 int panda_batch_size(const panda_batch *b);
 panda_ctx *panda_batch_context(panda_batch *b, int k);
+
+/* The phase-2 schedule autotuning of a tensor-core batch (no paper
+ * counterpart): *epi receives the epilogue weight of the schedule in use (MMA
+ * issue slots per tile), trial_ms[q] (n_trials entries, may be NULL) the
+ * phase-2 time of trial q in ms (0 while not yet run), *done whether the
+ * trials are over.  Returns the number of trial schedules, 0 for an FP32
+ * batch, PANDA_EINVAL for NULL b. */
+int panda_batch_schedule(const panda_batch *b, int *epi, float *trial_ms, int n_trials, int *done);
 
 const char *panda_batch_last_error(const panda_batch *b);
 void panda_batch_destroy(panda_batch *b);

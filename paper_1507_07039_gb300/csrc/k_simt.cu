@@ -259,14 +259,15 @@ __device__ __forceinline__ void fp8_norm_max(unsigned *slot, float v)
 
 // rsqW[i] = sum_b wrow_part[b][i], csqW[j] = sum_b wcol_part[b][j] (FP64).
 // Blocks [0, ceil(T/32)) take rows of W, the rest its columns.
-__global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_reduce_wnorms(Dev d)
+// block b of one network's launch: b < ceil(T/32) rows of W, the rest its columns
+__device__ __forceinline__ void reduce_wnorms_block(const Dev &d, int b)
 {
     if (!d.ctl->active)
         return;
     __shared__ double sh[1][RS_GROUPS][RS_ROWS];
     const int bT = ceil_div(d.T, RS_ROWS);
-    const bool rows = (int)blockIdx.x < bT;
-    const int x = ((rows ? blockIdx.x : blockIdx.x - bT) * RS_ROWS) + (threadIdx.x & (RS_ROWS - 1));
+    const bool rows = b < bT;
+    const int x = ((rows ? b : b - bT) * RS_ROWS) + (threadIdx.x & (RS_ROWS - 1));
     const bool ok = x < (rows ? d.T : d.G);
     const float *const src[1] = {rows ? d.wrow_part : d.wcol_part};
     double out[1];
@@ -277,6 +278,18 @@ __global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_reduce_wnorms(Dev d)
         (rows ? d.rsqW : d.csqW)[x] = (float)out[0];
     if (d.fp8)
         fp8_norm_max(&d.f8n[rows ? 2 : 3], ok ? (float)out[0] : 0.0f);
+}
+
+__global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_reduce_wnorms(const __grid_constant__ Dev d)
+{
+    reduce_wnorms_block(d, blockIdx.x);
+}
+
+// a set of networks: blocks[blockIdx.x] = (network, its block)
+__global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_reduce_wnorms_set(const Dev *devs, const int2 *blocks)
+{
+    const int2 w = blocks[blockIdx.x];
+    reduce_wnorms_block(devs[w.x], w.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -408,15 +421,16 @@ __global__ void __launch_bounds__(NT, 2) k_phase2(Dev d, int cur)
 // row partial sums added by 8 threads per row).  Blocks [0, ceil(T/32)) take
 // rows of P, the rest rows of C.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_fin(Dev d)
+// block b of one network's launch: b < ceil(T/32) rows of P, the rest rows of C
+__device__ __forceinline__ void fin_block(const Dev &d, int b)
 {
     const Ctl *ctl = d.ctl;
     if (!ctl->active)
         return;
     __shared__ double sh[3][RS_GROUPS][RS_ROWS];
     const int bT = ceil_div(d.T, RS_ROWS);
-    const bool isP = (int)blockIdx.x < bT;
-    const int i = ((isP ? blockIdx.x : blockIdx.x - bT) * RS_ROWS) + (threadIdx.x & (RS_ROWS - 1));
+    const bool isP = b < bT;
+    const int i = ((isP ? b : b - bT) * RS_ROWS) + (threadIdx.x & (RS_ROWS - 1));
     const int n = isP ? d.T : d.G;       // network size
     const bool ok = i < n;
     const int nb = isP ? (d.nsP ? d.nsP : d.nbT) : (d.nsC ? d.nsC : d.nbG);  // partial-sum slots
@@ -454,8 +468,19 @@ __global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_fin(Dev d)
         fp8_norm_max(&d.f8n[isP ? 0 : 1], nrm);
 }
 
-// h (Eq. 7), the counter and the stop test: one block.
-__global__ void k_tail(Dev d)
+__global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_fin(const __grid_constant__ Dev d)
+{
+    fin_block(d, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(RS_ROWS * RS_GROUPS) k_fin_set(const Dev *devs, const int2 *blocks)
+{
+    const int2 w = blocks[blockIdx.x];
+    fin_block(devs[w.x], w.y);
+}
+
+// h (Eq. 7), the counter and the stop test: one block per network.
+__device__ __forceinline__ void tail_block(const Dev &d)
 {
     Ctl *ctl = d.ctl;
     if (!ctl->active)
@@ -495,6 +520,10 @@ __global__ void k_tail(Dev d)
     }
 }
 
+__global__ void k_tail(const __grid_constant__ Dev d) { tail_block(d); }
+
+__global__ void k_tail_set(const Dev *devs) { tail_block(devs[blockIdx.x]); }
+
 }  // namespace
 
 const char *const SIMT_KERNEL_NAMES[SIMT_KERNELS] = {"k_rn", "k_phase1", "k_reduce_wnorms",
@@ -505,6 +534,21 @@ cudaError_t launch_reduce_wnorms(const Dev &d, cudaStream_t s)
     k_reduce_wnorms<<<ceil_div(d.T, RS_ROWS) + ceil_div(d.G, RS_ROWS), RS_ROWS * RS_GROUPS, 0, s>>>(d);
     return cudaGetLastError();
 }
+
+cudaError_t launch_reduce_wnorms_set(const Dev *devs, const int2 *blocks, int nblocks, cudaStream_t s)
+{
+    k_reduce_wnorms_set<<<nblocks, RS_ROWS * RS_GROUPS, 0, s>>>(devs, blocks);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fin_tail_set(const Dev *devs, const int2 *blocks, int nblocks, int nnets, cudaStream_t s)
+{
+    k_fin_set<<<nblocks, RS_ROWS * RS_GROUPS, 0, s>>>(devs, blocks);
+    k_tail_set<<<nnets, 256, 0, s>>>(devs);
+    return cudaGetLastError();
+}
+
+int set_norm_blocks(int T, int G) { return ceil_div(T, RS_ROWS) + ceil_div(G, RS_ROWS); }
 
 cudaError_t launch_fin_tail(const Dev &d, cudaStream_t s, KernelEvents &ke)
 {

@@ -56,6 +56,22 @@ struct TcMaps {  // split copies, K-major, boxes of 64 x 128 (one CTA's half of 
     CUtensorMap W8[2], Wt8[2], C8;   // FP8MIX: E4M3 copies, boxes of 128 B x 128 rows
 };
 
+// A set of networks iterated by one launch per phase (device arrays, one entry per network)
+struct SetArgs {
+    const Dev *devs;       // the networks' device state
+    const TcMaps *maps;    // their tensor maps (64-byte aligned, in global memory)
+    const int *parity;     // W buffer of a network = (parity + its iteration count) & 1
+    const int4 *items1;    // phase 1: one (network, mt, nt, 0) per CTA pair
+    const int *sched_off;  // phase 2: per CTA pair, its range of sched
+    const int *sched;      // phase 2: packed tiles (as for one network)
+    const int *sched_net;  // phase 2: the network of each tile
+};
+
+__device__ __forceinline__ int set_cur(const SetArgs &a, int net)
+{
+    return (a.parity[net] + a.devs[net].ctl->iters) & 1;
+}
+
 __device__ __forceinline__ uint8_t *align1024(uint8_t *p)
 {
     return reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
@@ -452,8 +468,10 @@ constexpr size_t phase1_smem()
            (P1_COLVEC + P1_COLRED + P1_ROWRED + EPI1 * P1_BLK) * sizeof(float) + EPI1 * sizeof(double);
 }
 
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
-    k_tc_phase1(const __grid_constant__ TcMaps maps, Dev d, int cur)
+// The body of phase 1 for the tile (mt, nt) of one network: maps and d are
+// that network's (kernel parameters for one network, entries of arrays in
+// global memory for a set), cur its current W buffer.
+__device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, int cur, int mt, int nt)
 {
     Ctl *ctl = d.ctl;
     if (!ctl->active)  // both CTAs of a pair see the same value and leave together
@@ -469,7 +487,6 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
-    const int mt = blockIdx.x >> 1, nt = blockIdx.y;
     const int m0 = mt * 256 + 128 * (int)rank;  // this CTA's 128 rows (TFs)
     const int n0 = nt * 256;                    // the tile's 256 columns (genes)
     // k-blocks: R-num over TFs (64 BF16 per row), then A-num over genes (64 BF16, or 128 E4M3 under FP8MIX)
@@ -588,7 +605,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
         // FP8MIX: the A-num accumulator holds the scaled E4M3 products; W' gets E4M3 copies too
         const bool q8 = d.fp8 != 0;
         const float ainv = q8 ? 1.0f / (d.f8[cur] * d.f8[2]) : 1.0f, s8 = q8 ? d.f8[3] : 1.0f;
-        if (q8 && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 64)
+        if (q8 && mt == 0 && nt == 0 && rank == 0 && threadIdx.x == 64)
             d.f8[nx] = s8;  // the scale of W8[nx] and Wt8[nx] from here on
         // what does not depend on the accumulators is fetched before waiting for them
         {
@@ -720,6 +737,22 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
     }
 }
 
+
+// One network: a grid of 2 x (Tp / 256) by Gp / 256 CTAs, one pair per tile.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
+    k_tc_phase1(const __grid_constant__ TcMaps maps, const __grid_constant__ Dev d, int cur)
+{
+    phase1_tile(maps, d, cur, blockIdx.x >> 1, blockIdx.y);
+}
+
+// A set of networks: one pair per entry of the work list, each entry a tile of one network.
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1) k_tc_phase1_set(const SetArgs a)
+{
+    const int4 w = a.items1[blockIdx.x >> 1];  // (network, mt, nt, -)
+    const Dev &d = a.devs[w.x];
+    phase1_tile(a.maps[w.x], d, set_cur(a, w.x), w.y, w.z);
+}
+
 // ---------------------------------------------------------------------------
 // Phase 2: persistent CTA pairs over a host-built schedule of upper-triangle
 // 256 x 256 tiles of W'.W'^T (P, K = genes) and W'^T.W' (C, K = TFs).  In a
@@ -769,14 +802,37 @@ constexpr size_t phase2_smem()
            (C::COLRED + C::ROWRED + C::COLNRM + EPI2 * C::BLK) * sizeof(float);
 }
 
-template <bool SIM_SIGMA>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
-    k_tc_phase2(const __grid_constant__ TcMaps maps, Dev d, int cur, const int *__restrict__ sched_off,
-                const int *__restrict__ sched)
+// Where phase 2 finds the network of each scheduled tile: one network given
+// by value (its state, maps and W buffer are kernel parameters), or a set.
+struct P2One {
+    const TcMaps &m;
+    const Dev &d;
+    int c;
+    const int *off, *tiles;
+    __device__ int net(int) const { return 0; }
+    __device__ const Dev &dev(int) const { return d; }
+    __device__ const TcMaps &maps(int) const { return m; }
+    __device__ int cur(int) const { return c; }  // the W' buffer (the launch passes it)
+    __device__ bool active(int) const { return true; }  // the kernel left at once otherwise
+};
+struct P2Set {
+    const SetArgs &a;
+    const int *off, *tiles;
+    __device__ int net(int n) const { return a.sched_net[n]; }
+    __device__ const Dev &dev(int k) const { return a.devs[k]; }
+    __device__ const TcMaps &maps(int k) const { return a.maps[k]; }
+    // phase 2 works on W' (the other buffer: the count moves on only in k_tail)
+    __device__ int cur(int k) const { return set_cur(a, k) ^ 1; }
+    __device__ bool active(int k) const { return a.devs[k].ctl->active != 0; }
+};
+
+// The body of phase 2 for one CTA pair's scheduled tiles.  A stopped network's
+// tiles are skipped by every role alike (its control block does not change
+// during the launch), so the stage and accumulator counters stay in step.
+// ctl: where a timed-out wait outside any tile is reported.
+template <bool SIM_SIGMA, class Src>
+__device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
 {
-    Ctl *ctl = d.ctl;
-    if (!ctl->active)  // both CTAs of a pair see the same value and leave together
-        return;
     using Cfg = P2Cfg<SIM_SIGMA>;
     constexpr int ST2 = Cfg::ST, NS = Cfg::NS;
     using Sync2 = Sync2T<ST2>;
@@ -791,7 +847,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = cluster_ctarank();
     const int pair = blockIdx.x >> 1;
-    const int first = sched_off[pair], last = sched_off[pair + 1];
+    const int first = src.off[pair], last = src.off[pair + 1];
 
     if (threadIdx.x == 0) {
         for (int q = 0; q < ST2; ++q) {
@@ -818,7 +874,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             int g = 0;
             bool ok = true;
             for (int n = first; n < last && ok; ++n) {
-                const int tile = sched[n];
+                const int net = src.net(n);
+                if (!src.active(net))
+                    continue;
+                const Dev &d = src.dev(net);
+                const TcMaps &maps = src.maps(net);
+                const int cur = src.cur(net);
+                const int tile = src.tiles[n];
                 const bool isP = tile < 0;
                 const int m0 = ((tile >> 16) & 0x7fff) * N2 + 128 * rank, n0 = (tile & 0xffff) * N2 + 128 * rank;
                 const bool q8 = d.fp8 && !isP;  // FP8MIX: C tiles from the E4M3 copy of W'^T, one term
@@ -827,7 +889,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                 const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl[cur];
                 for (int kb = 0; kb < nk; ++kb, ++g) {
                     const int st = g % ST2;
-                    if (!wait_bounded(&sy.empty[st], ((uint32_t)(g / ST2) & 1u) ^ 1u, &sy.abort, ctl)) {
+                    if (!wait_bounded(&sy.empty[st], ((uint32_t)(g / ST2) & 1u) ^ 1u, &sy.abort, d.ctl)) {
                         ok = false;
                         break;
                     }
@@ -854,18 +916,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
             constexpr uint32_t idesc = idesc_bf16_f32(256, N2);
             int g = 0;
             bool ok = true;
-            for (int n = first, idx = 0; n < last && ok; ++n, ++idx) {
-                const int tile = sched[n];
+            for (int n = first, idx = -1; n < last && ok; ++n) {
+                const int net = src.net(n);
+                if (!src.active(net))
+                    continue;
+                ++idx;
+                const Dev &d = src.dev(net);
+                const int tile = src.tiles[n];
                 const bool q8 = d.fp8 && tile >= 0;
                 const int nk = tile < 0 ? d.Gp / BK : d.Tp / (q8 ? 2 * BK : BK);
                 const int buf = idx & 1;
-                if (!wait_bounded(&sy.tempty[buf], ((uint32_t)(idx >> 1) & 1u) ^ 1u, &sy.abort, ctl))
+                if (!wait_bounded(&sy.tempty[buf], ((uint32_t)(idx >> 1) & 1u) ^ 1u, &sy.abort, d.ctl))
                     break;
                 tc_fence_after();
                 const uint32_t dacc = sy.tmem + buf * N2;
                 for (int kb = 0; kb < nk; ++kb, ++g) {
                     const int st = g % ST2;
-                    if (!wait_bounded(&sy.full[st], (uint32_t)(g / ST2) & 1u, &sy.abort, ctl)) {
+                    if (!wait_bounded(&sy.full[st], (uint32_t)(g / ST2) & 1u, &sy.abort, d.ctl)) {
                         ok = false;
                         break;
                     }
@@ -906,17 +973,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
         const int r = wq * 32 + lane;  // row of this CTA's 128-row half
         float *blk = blocks + (size_t)e * Cfg::BLK;  // this warp's 32 x 16 staging block, rows of 17
         const int tt = threadIdx.x - 64;  // 0..383
-        const float a = ctl->alpha, keep = 1.0f - a;
         const uint32_t tempty_even = mapa_shared(smem_u32(&sy.tempty[0]), 0);
-        // FP8MIX: C-tile accumulators hold products of W'^T scaled by f8[cur] on both sides; C' gets
-        // an E4M3 copy scaled so that no entry saturates (bound from |C_k.| and |W'_.k|)
-        const float sw = d.fp8 ? d.f8[cur] : 1.0f, ainv2 = 1.0f / (sw * sw);
-        const float sC = d.fp8 ? e4m3_scale(fp8_bound_c(__uint_as_float(d.f8n[5]), __uint_as_float(d.f8n[3])))
-                               : 1.0f;
-        if (d.fp8 && blockIdx.x == 0 && threadIdx.x == 64)
-            d.f8[2] = sC;  // the scale of C8 from here on
-        for (int n = first, idx = 0; n < last; ++n, ++idx) {
-            const int tile = sched[n];
+        for (int n = first, idx = -1; n < last; ++n) {
+            const int net = src.net(n);
+            if (!src.active(net))
+                continue;
+            ++idx;
+            const Dev &d = src.dev(net);
+            const int cur = src.cur(net);
+            const float a = d.ctl->alpha, keep = 1.0f - a;
+            // FP8MIX: C-tile accumulators hold products of W'^T scaled by f8[cur] on both sides; C' gets
+            // an E4M3 copy scaled so that no entry saturates (bound from |C_k.| and |W'_.k|)
+            const float sw = d.fp8 ? d.f8[cur] : 1.0f, ainv2 = 1.0f / (sw * sw);
+            const float sC =
+                d.fp8 ? e4m3_scale(fp8_bound_c(__uint_as_float(d.f8n[5]), __uint_as_float(d.f8n[3]))) : 1.0f;
+            if (d.fp8 && threadIdx.x == 64)
+                d.f8[2] = sC;  // the scale of C8 from here on (every writer stores the same value)
+            const int tile = src.tiles[n];
             const bool isP = tile < 0;
             const int bm = (tile >> 16) & 0x7fff, bn = tile & 0xffff;
             const int m0 = bm * N2 + 128 * (int)rank, n0 = bn * N2;
@@ -948,7 +1021,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
                 ld_rows4(xblk + c_begin * 16, ld, nxt);
             epi_bar_p2();
             // on a timed-out wait every epilogue warp still runs the named barriers below
-            const bool live = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, ctl) &&
+            const bool live = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, d.ctl) &&
                               !*(volatile int *)&sy.abort;
             tc_fence_after();
             float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
@@ -1193,6 +1266,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
     }
 }
 
+template <bool SIM_SIGMA>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
+    k_tc_phase2(const __grid_constant__ TcMaps maps, const __grid_constant__ Dev d, int cur,
+                const int *__restrict__ sched_off, const int *__restrict__ sched)
+{
+    if (!d.ctl->active)  // both CTAs of a pair see the same value and leave together
+        return;
+    phase2_pair<SIM_SIGMA>(P2One{maps, d, cur, sched_off, sched}, d.ctl);
+}
+
+template <bool SIM_SIGMA>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1) k_tc_phase2_set(const SetArgs a)
+{
+    phase2_pair<SIM_SIGMA>(P2Set{a, a.sched_off, a.sched}, a.devs[0].ctl);
+}
+
+// every network's control block into one array (one read-back per chunk of a set)
+__global__ void k_gather_ctl(const Dev *devs, int n, Ctl *out)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n)
+        out[k] = *devs[k].ctl;
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -1253,41 +1350,71 @@ struct TcHost {
     int grid2 = 0;
 };
 
-// Longest-processing-time assignment of the upper-triangle 256 x 256 tiles of
-// P and C to `ctas` persistent CTA pairs; cost of a tile = its k-blocks + a
-// fixed epilogue share.
-void build_schedule(const Dev &d, int ctas, std::vector<int> &off, std::vector<int> &tiles)
+// Cost of a phase-2 tile in MMA issue slots (a BF16 MMA of K = 16 and an E4M3
+// MMA of K = 32 take the same time) plus a fixed epilogue share.
+int tile_cost(const Dev &d, bool isP, int epi)
 {
-    struct T_ { int cost, code; };
+    const int terms = d.split_b ? 3 : 2;
+    if (isP)
+        return (d.Gp / BK) * 4 * terms + epi;
+    if (d.fp8)
+        return (d.Tp / (2 * BK)) * 4 + epi;
+    return (d.Tp / BK) * 4 * terms + epi;
+}
+
+// Longest-processing-time assignment of the upper-triangle 256 x 256 tiles of
+// P and C of every network to `pairs` persistent CTA pairs.  Outputs: per pair
+// a range off[p] .. off[p + 1] of tiles (packed: bit 31 = P, bits 16-30 = row
+// block, bits 0-15 = column block) and nets (the network of each tile).  The
+// order of tiles within a pair's list is the order they were assigned
+// (longest first); their results do not depend on the assignment.
+void build_schedule_set(const std::vector<const Dev *> &ds, int pairs, int epi, std::vector<int> &off,
+                        std::vector<int> &tiles, std::vector<int> &nets)
+{
+    struct T_ { int cost, code, net; };
     std::vector<T_> all;
-    const int kP = d.Gp / BK, kC = d.Tp / BK, epi = 16;
-    const int nbP = ceil_div(d.Tp, N2), nbC = ceil_div(d.Gp, N2);
-    for (int bm = 0; bm < nbP; ++bm)
-        for (int bn = bm; bn < nbP; ++bn)
-            all.push_back({kP + epi, (int)(0x80000000u | ((uint32_t)bm << 16) | (uint32_t)bn)});
-    for (int bm = 0; bm < nbC; ++bm)
-        for (int bn = bm; bn < nbC; ++bn)
-            all.push_back({kC + epi, (bm << 16) | bn});
+    for (int k = 0; k < (int)ds.size(); ++k) {
+        const Dev &d = *ds[k];
+        const int nbP = ceil_div(d.Tp, N2), nbC = ceil_div(d.Gp, N2);
+        const int cP = tile_cost(d, true, epi), cC = tile_cost(d, false, epi);
+        for (int bm = 0; bm < nbP; ++bm)
+            for (int bn = bm; bn < nbP; ++bn)
+                all.push_back({cP, (int)(0x80000000u | ((uint32_t)bm << 16) | (uint32_t)bn), k});
+        for (int bm = 0; bm < nbC; ++bm)
+            for (int bn = bm; bn < nbC; ++bn)
+                all.push_back({cC, (bm << 16) | bn, k});
+    }
     std::stable_sort(all.begin(), all.end(), [](const T_ &a, const T_ &b) { return a.cost > b.cost; });
-    if (ctas > (int)all.size())
-        ctas = (int)all.size();
-    std::vector<std::vector<int>> lists(ctas);
+    if (pairs > (int)all.size())
+        pairs = (int)all.size();
+    std::vector<std::vector<std::pair<int, int>>> lists(pairs);
     using L = std::pair<long long, int>;
     std::priority_queue<L, std::vector<L>, std::greater<L>> heap;
-    for (int c = 0; c < ctas; ++c)
+    for (int c = 0; c < pairs; ++c)
         heap.push({0, c});
     for (const auto &t : all) {
         L top = heap.top();
         heap.pop();
-        lists[top.second].push_back(t.code);
+        lists[top.second].push_back({t.code, t.net});
         heap.push({top.first + t.cost, top.second});
     }
     off.assign(1, 0);
     tiles.clear();
+    nets.clear();
     for (const auto &l : lists) {
-        tiles.insert(tiles.end(), l.begin(), l.end());
+        for (const auto &t : l) {
+            tiles.push_back(t.first);
+            nets.push_back(t.second);
+        }
         off.push_back((int)tiles.size());
     }
+}
+
+// One network, epilogue weight of 16 BF16X3 k-blocks (192 MMA slots).
+void build_schedule(const Dev &d, int pairs, std::vector<int> &off, std::vector<int> &tiles)
+{
+    std::vector<int> nets;
+    build_schedule_set({&d}, pairs, 192, off, tiles, nets);
 }
 
 cudaError_t set_smem_limits()
@@ -1296,7 +1423,13 @@ cudaError_t set_smem_limits()
     if (done)
         return cudaSuccess;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_tc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phase1_smem())))
+    if ((e = cudaFuncSetAttribute(k_tc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phase1_smem())) ||
+        (e = cudaFuncSetAttribute(k_tc_phase1_set, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)phase1_smem())) ||
+        (e = cudaFuncSetAttribute(k_tc_phase2_set<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)phase2_smem<false>())) ||
+        (e = cudaFuncSetAttribute(k_tc_phase2_set<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)phase2_smem<true>())))
         return e;
     if ((e = cudaFuncSetAttribute(k_tc_phase2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)phase2_smem<false>())))
@@ -1425,6 +1558,137 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
         k_tc_phase2<false><<<h.grid2, THREADS2, phase2_smem<false>(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
     ke.mark(s);
     return launch_fin_tail(d, s, ke);
+}
+
+// ---- sets of networks: one launch per phase over all networks' tiles ---------------
+struct TcSet {
+    int n = 0, diag = 0;
+    Dev *devs = nullptr;      // device copies of the networks' Dev
+    TcMaps *maps = nullptr;   // their tensor maps
+    int *parity = nullptr;
+    int4 *items1 = nullptr;
+    int nitems1 = 0;
+    int2 *blocks = nullptr;
+    int nblocks = 0;
+    Ctl *gather = nullptr;
+    struct Cand {
+        int epi = 0, pairs = 0;
+        int *off = nullptr, *tiles = nullptr, *nets = nullptr;
+    };
+    std::vector<Cand> cands;  // phase-2 schedules, one per epilogue weight
+};
+
+namespace {
+template <class T>
+cudaError_t upload(T **dst, const std::vector<T> &v)
+{
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, v.size()) * sizeof(T));
+    if (!e && !v.empty())
+        e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+}  // namespace
+
+const int TC_SET_EPI[TC_SET_CANDS] = {48, 96, 192, 384, 768};
+
+cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out)
+{
+    *out = nullptr;
+    cudaError_t e = set_smem_limits();
+    if (e)
+        return e;
+    TcSet *t = new TcSet;
+    t->n = (int)ds.size();
+    t->diag = ds[0]->diag;
+    std::vector<Dev> hd;
+    std::vector<TcMaps> hm;
+    std::vector<int4> it;
+    std::vector<int2> bl;
+    for (int k = 0; k < t->n; ++k) {
+        const Dev &d = *ds[k];
+        hd.push_back(d);
+        hm.push_back(static_cast<const TcHost *>(d.tc_host)->maps);
+        for (int mt = 0; mt < d.Tp / 256; ++mt)
+            for (int nt = 0; nt < d.Gp / 256; ++nt)
+                it.push_back(make_int4(k, mt, nt, d.Tp / BK + d.Gp / (d.fp8 ? 2 * BK : BK)));
+        for (int b = 0; b < set_norm_blocks(d.T, d.G); ++b)
+            bl.push_back(make_int2(k, b));
+    }
+    // the block scheduler starts pairs in index order: longest main loops first
+    std::stable_sort(it.begin(), it.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
+    t->nitems1 = (int)it.size();
+    t->nblocks = (int)bl.size();
+    int dev = 0, nsm = 0;
+    if (!(e = cudaGetDevice(&dev)) && !(e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) &&
+        !(e = upload(&t->devs, hd)) && !(e = upload(&t->maps, hm)) && !(e = upload(&t->items1, it)) &&
+        !(e = upload(&t->blocks, bl)) && !(e = cudaMalloc(&t->parity, t->n * sizeof(int))) &&
+        !(e = cudaMemset(t->parity, 0, t->n * sizeof(int))) && !(e = cudaMalloc(&t->gather, t->n * sizeof(Ctl)))) {
+        for (int q = 0; q < TC_SET_CANDS && !e; ++q) {
+            std::vector<int> off, tiles, nets;
+            build_schedule_set(ds, nsm / 2, TC_SET_EPI[q], off, tiles, nets);
+            TcSet::Cand c;
+            c.epi = TC_SET_EPI[q];
+            c.pairs = (int)off.size() - 1;
+            if (!(e = upload(&c.off, off)) && !(e = upload(&c.tiles, tiles)))
+                e = upload(&c.nets, nets);
+            t->cands.push_back(c);
+        }
+    }
+    if (e) {
+        tc_set_destroy(t);
+        return e;
+    }
+    *out = t;
+    return cudaSuccess;
+}
+
+cudaError_t tc_set_parity(TcSet *t, const std::vector<int> &parity, cudaStream_t s)
+{
+    return cudaMemcpyAsync(t->parity, parity.data(), t->n * sizeof(int), cudaMemcpyHostToDevice, s);
+}
+
+cudaError_t tc_set_launch(TcSet *t, int cand, cudaStream_t s, cudaEvent_t p2_begin, cudaEvent_t p2_end)
+{
+    const TcSet::Cand &c = t->cands[cand];
+    SetArgs a{t->devs, t->maps, t->parity, t->items1, c.off, c.tiles, c.nets};
+    k_tc_phase1_set<<<2 * t->nitems1, THREADS1, phase1_smem(), s>>>(a);
+    cudaError_t e = launch_reduce_wnorms_set(t->devs, t->blocks, t->nblocks, s);
+    if (e)
+        return e;
+    if (p2_begin)
+        cudaEventRecord(p2_begin, s);
+    if (t->diag == 2)
+        k_tc_phase2_set<true><<<2 * c.pairs, THREADS2, phase2_smem<true>(), s>>>(a);
+    else
+        k_tc_phase2_set<false><<<2 * c.pairs, THREADS2, phase2_smem<false>(), s>>>(a);
+    if (p2_end)
+        cudaEventRecord(p2_end, s);
+    return launch_fin_tail_set(t->devs, t->blocks, t->nblocks, t->n, s);
+}
+
+cudaError_t tc_set_gather(TcSet *t, Ctl *host, cudaStream_t s)
+{
+    k_gather_ctl<<<ceil_div(t->n, 128), 128, 0, s>>>(t->devs, t->n, t->gather);
+    cudaError_t e = cudaGetLastError();
+    return e ? e : cudaMemcpyAsync(host, t->gather, t->n * sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+}
+
+void tc_set_destroy(TcSet *t)
+{
+    if (!t)
+        return;
+    cudaFree(t->devs);
+    cudaFree(t->maps);
+    cudaFree(t->parity);
+    cudaFree(t->items1);
+    cudaFree(t->blocks);
+    cudaFree(t->gather);
+    for (auto &c : t->cands) {
+        cudaFree(c.off);
+        cudaFree(c.tiles);
+        cudaFree(c.nets);
+    }
+    delete t;
 }
 
 // D = A . B^T on the tensor-core pipeline (self-test support)

@@ -920,7 +920,158 @@ void panda_destroy(panda_ctx *c)
 struct panda_batch {
     std::vector<panda_ctx *> nets;
     std::string err;
+    // tensor-core modes: the set engine (one launch per phase for all networks)
+    TcSet *set = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int graph_iters = 8;
+    Ctl *h_ctls = nullptr;               // pinned: every network's control block after a chunk
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    int tune_next = 0;                   // phase-2 schedule autotuning: next trial (warm-up first)
+    int chosen = 2;                      // the schedule in use (an index into TC_SET_EPI)
+    float tune_ms[TC_SET_CANDS] = {};
 };
+
+namespace {
+void batch_free_set(panda_batch *b)
+{
+    if (b->gexec)
+        cudaGraphExecDestroy(b->gexec);
+    tc_set_destroy(b->set);
+    if (b->h_ctls)
+        cudaFreeHost(b->h_ctls);
+    for (cudaEvent_t &e : b->ev)
+        if (e)
+            cudaEventDestroy(e);
+    if (b->stream)
+        cudaStreamDestroy(b->stream);
+    b->set = nullptr;
+    b->gexec = nullptr;
+    b->h_ctls = nullptr;
+    b->stream = nullptr;
+}
+
+// The set engine's graph: graph_iters iterations of every network, the chosen schedule.
+int batch_graph(panda_batch *b)
+{
+    if (b->gexec)
+        return 0;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    for (int k = 0; k < b->graph_iters && !e; ++k)
+        e = tc_set_launch(b->set, b->chosen, b->stream, nullptr, nullptr);
+    cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+    if (!e)
+        e = e2;
+    if (!e)
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+    if (g)
+        cudaGraphDestroy(g);
+    if (e) {
+        b->gexec = nullptr;
+        b->err = std::string("set graph: ") + cudaGetErrorString(e);
+        return PANDA_ECUDA;
+    }
+    return 0;
+}
+
+// One chunk of the set engine: while the schedule autotuning is unfinished, a
+// single iteration with the next trial schedule, its phase 2 timed (trial 0
+// warms up with the default schedule; trials 1.. time each candidate, then the
+// fastest is kept); afterwards the captured graph.  Every schedule gives the
+// same results.  Then all control blocks are read back.
+int batch_chunk(panda_batch *b)
+{
+    cudaError_t e;
+    const bool tuning = b->tune_next <= TC_SET_CANDS;
+    if (tuning) {
+        const int trial = b->tune_next;
+        const int cand = trial == 0 ? b->chosen : trial - 1;
+        if ((e = tc_set_launch(b->set, cand, b->stream, b->ev[0], b->ev[1])))
+            return b->err = std::string("set launch: ") + cudaGetErrorString(e), PANDA_ECUDA;
+    } else {
+        int rc = batch_graph(b);
+        if (rc)
+            return rc;
+        if ((e = cudaGraphLaunch(b->gexec, b->stream)))
+            return b->err = std::string("set graph launch: ") + cudaGetErrorString(e), PANDA_ECUDA;
+    }
+    if ((e = tc_set_gather(b->set, b->h_ctls, b->stream)) || (e = cudaStreamSynchronize(b->stream)))
+        return b->err = std::string("set chunk: ") + cudaGetErrorString(e), PANDA_ECUDA;
+    if (tuning) {
+        const int trial = b->tune_next++;
+        float ms = 0.0f;
+        if ((e = cudaEventElapsedTime(&ms, b->ev[0], b->ev[1])))
+            return b->err = std::string("set timing: ") + cudaGetErrorString(e), PANDA_ECUDA;
+        if (trial > 0)
+            b->tune_ms[trial - 1] = ms;
+        if (trial == TC_SET_CANDS) {
+            int best = 0;
+            for (int q = 1; q < TC_SET_CANDS; ++q)
+                if (b->tune_ms[q] < b->tune_ms[best])
+                    best = q;
+            b->chosen = best;
+        }
+    }
+    return 0;
+}
+
+int batch_run_set(panda_batch *b, float alpha, double tol, int max_iter, int *iters_out, double *h_last)
+{
+    const size_t n = b->nets.size();
+    std::vector<DriveState> ds(n);
+    std::vector<int> parity(n);
+    for (size_t k = 0; k < n; ++k) {  // arm every control block, as a single run does
+        panda_ctx *c = b->nets[k];
+        int rc = drive_begin(c, alpha, tol, max_iter, false, ds[k]);
+        if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess)
+            rc = set_err(c, PANDA_ECUDA, "stream synchronize failed");
+        if (rc) {
+            b->err = "network " + std::to_string(k) + ": " + c->err;
+            return rc;
+        }
+        parity[k] = (c->cur - ds[k].start) & 1;
+    }
+    cudaError_t e = tc_set_parity(b->set, parity, b->stream);
+    if (e)
+        return b->err = std::string("set parity: ") + cudaGetErrorString(e), PANDA_ECUDA;
+    bool any = max_iter > 0;
+    int rc = 0;
+    while (any && !rc) {
+        if ((rc = batch_chunk(b)))
+            break;
+        any = false;
+        for (size_t k = 0; k < n; ++k)
+            any = any || b->h_ctls[k].active;
+    }
+    if (rc) {
+        cudaStreamSynchronize(b->stream);
+        return rc;
+    }
+    bool all = true;
+    for (size_t k = 0; k < n; ++k) {
+        panda_ctx *c = b->nets[k];
+        if (max_iter > 0)
+            *c->h_ctl = b->h_ctls[k];
+        const Ctl &h = *c->h_ctl;
+        c->cur ^= ((h.iters - ds[k].start) & 1);
+        if (h.status & ST_NONFINITE)
+            rc = set_err(c, PANDA_ENONFINITE, "the state became non-finite");
+        else if (h.status & ST_TIMEOUT)
+            rc = set_err(c, PANDA_ETIMEOUT, "a bounded device wait expired");
+        if (rc) {
+            b->err = "network " + std::to_string(k) + ": " + c->err;
+            return rc;
+        }
+        if (iters_out)
+            iters_out[k] = h.iters - ds[k].start;
+        if (h_last)
+            h_last[k] = h.h_last;
+        all = all && h.converged;
+    }
+    return all ? PANDA_OK : PANDA_NOT_CONVERGED;
+}
+}  // namespace
 
 int panda_batch_create(panda_batch **out, int n, const int *T, const int *G, const float *const *W0,
                        const float *const *P0, const float *const *C0, const panda_opts *o)
@@ -943,6 +1094,27 @@ int panda_batch_create(panda_batch **out, int n, const int *T, const int *G, con
         }
         b->nets.push_back(c);
     }
+    if (tensor_prec(b->nets[0]->prec)) {  // the set engine
+        std::vector<const Dev *> ds;
+        for (panda_ctx *c : b->nets)
+            ds.push_back(&c->d);
+        b->graph_iters = b->nets[0]->graph_iters > 0 ? b->nets[0]->graph_iters : 2;
+        cudaError_t e = tc_set_create(ds, &b->set);
+        if (!e)
+            e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (!e)
+            e = cudaMallocHost(&b->h_ctls, n * sizeof(Ctl));
+        for (int q = 0; q < 2 && !e; ++q)
+            e = cudaEventCreate(&b->ev[q]);
+        if (e) {
+            std::string msg = std::string("panda_batch_create: set engine: ") + cudaGetErrorString(e);
+            batch_free_set(b);
+            for (panda_ctx *x : b->nets)
+                panda_destroy(x);
+            delete b;
+            return set_err(nullptr, PANDA_ECUDA, msg);
+        }
+    }
     *out = b;
     return 0;
 }
@@ -955,6 +1127,8 @@ int panda_batch_run(panda_batch *b, float alpha, double tol, int max_iter, int *
         b->err = "alpha must be in [0, 1], tol >= 0 and max_iter >= 0";
         return PANDA_EINVAL;
     }
+    if (b->set)
+        return batch_run_set(b, alpha, tol, max_iter, iters_out, h_last);
     const size_t n = b->nets.size();
     std::vector<DriveState> ds(n);
     std::vector<char> more(n, max_iter > 0 ? 1 : 0);
@@ -1016,12 +1190,30 @@ panda_ctx *panda_batch_context(panda_batch *b, int k)
     return b->nets[k];
 }
 
+int panda_batch_schedule(const panda_batch *b, int *epi, float *trial_ms, int n_trials, int *done)
+{
+    if (!b)
+        return PANDA_EINVAL;
+    if (!b->set)
+        return 0;
+    if (epi)
+        *epi = TC_SET_EPI[b->chosen];
+    for (int q = 0; trial_ms && q < n_trials && q < TC_SET_CANDS; ++q)
+        trial_ms[q] = b->tune_ms[q];
+    if (done)
+        *done = b->tune_next > TC_SET_CANDS;
+    return TC_SET_CANDS;
+}
+
 const char *panda_batch_last_error(const panda_batch *b) { return b ? b->err.c_str() : g_create_error.c_str(); }
 
 void panda_batch_destroy(panda_batch *b)
 {
     if (!b)
         return;
+    if (b->stream)
+        cudaStreamSynchronize(b->stream);
+    batch_free_set(b);
     for (panda_ctx *c : b->nets)
         panda_destroy(c);
     delete b;

@@ -15,6 +15,7 @@
 
 #include <cuda_runtime.h>
 #include <cmath>
+#include <vector>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -149,6 +150,11 @@ cudaError_t launch_iteration_simt(const Dev &d, int cur, cudaStream_t s, KernelE
 cudaError_t launch_fin_tail(const Dev &d, cudaStream_t s, KernelEvents &ke);
 // FP64 sums of the per-tile norm partials of W' (shared by both paths)
 cudaError_t launch_reduce_wnorms(const Dev &d, cudaStream_t s);
+// The same kernels over a set of networks (device arrays): blocks[b] = (network,
+// that network's block), set_norm_blocks(T, G) blocks per network; one k_tail block per network.
+cudaError_t launch_reduce_wnorms_set(const Dev *devs, const int2 *blocks, int nblocks, cudaStream_t s);
+cudaError_t launch_fin_tail_set(const Dev *devs, const int2 *blocks, int nblocks, int nnets, cudaStream_t s);
+int set_norm_blocks(int T, int G);
 
 // ---- tensor-core path (k_tc.cu) --------------------------------------------
 constexpr int TC_KERNELS = 5;
@@ -158,6 +164,23 @@ bool tc_supported();
 cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales = true);  // split copies of the state, tensor maps
 void tc_release(Dev &d);
 cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
+
+// A set of networks (tensor-core modes, same options) iterated by one launch
+// per phase: phase 1 over every network's tiles, phase 2 persistent over an
+// LPT schedule of all their tiles, the norm and stop kernels over all their
+// rows.  Each network's W buffer is (parity + its iteration count) & 1.
+// Phase-2 schedules for TC_SET_CANDS epilogue weights are built; a tile's
+// result does not depend on which pair computes it, so any schedule gives the
+// same bits and the fastest can be picked by timing real iterations.
+struct TcSet;
+constexpr int TC_SET_CANDS = 5;
+extern const int TC_SET_EPI[TC_SET_CANDS];
+cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out);
+cudaError_t tc_set_parity(TcSet *t, const std::vector<int> &parity, cudaStream_t s);
+// one iteration of every active network; events (may be NULL) around phase 2
+cudaError_t tc_set_launch(TcSet *t, int cand, cudaStream_t s, cudaEvent_t p2_begin, cudaEvent_t p2_end);
+cudaError_t tc_set_gather(TcSet *t, Ctl *host, cudaStream_t s);  // all control blocks to host (async)
+void tc_set_destroy(TcSet *t);
 // D (M x N, row-major) = A (M x K) . B (N x K)^T through the tcgen05 pipeline,
 // host buffers; terms = 1 (hi only) or 3 (split).  *status: device status bits.
 // stall_kb >= 0 plants a stage whose loads are never issued (timeout test).

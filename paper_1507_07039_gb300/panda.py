@@ -73,6 +73,7 @@ def _load() -> ctypes.CDLL:
         "panda_batch_size": (i, [vp]),
         "panda_batch_context": (vp, [vp, i]),
         "panda_batch_last_error": (ctypes.c_char_p, [vp]),
+        "panda_batch_schedule": (i, [vp, pi, ctypes.POINTER(ctypes.c_float), i, pi]),
         "panda_batch_destroy": (None, [vp]),
         "panda_destroy": (None, [vp]),
     }
@@ -401,6 +402,16 @@ class PandaBatch:
     def context(self, k):
         """Network k's context handle (owned by the batch)."""
         return ctypes.c_void_p(lib.panda_batch_context(self.h, int(k)))
+
+    def schedule(self):
+        """(epilogue weight in use, trial times in ms, trials done) of the
+        phase-2 schedule autotuning; None for an FP32 batch."""
+        epi, done = ctypes.c_int(0), ctypes.c_int(0)
+        ms = (ctypes.c_float * 16)()
+        n = lib.panda_batch_schedule(self.h, ctypes.byref(epi), ms, 16, ctypes.byref(done))
+        if n < 0:
+            raise PandaError(n, "panda_batch_schedule")
+        return None if n == 0 else (epi.value, [ms[q] for q in range(n)], bool(done.value))
 
     def close(self):
         if self.h:

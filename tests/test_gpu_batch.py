@@ -1,5 +1,8 @@
 """Sets of networks (panda_batch_*): each network of an uneven set must match
-the same network run alone (bit for bit) and the FP64 oracle (needs a GB300)."""
+the same network run alone (bit for bit) and the FP64 oracle (needs a GB300).
+In the tensor-core modes the set runs as one launch per phase over every
+network's tiles, with the phase-2 schedule picked by timing real iterations;
+any schedule gives the same bits."""
 from __future__ import annotations
 
 import os
@@ -20,7 +23,7 @@ def uneven_set(count=5, seed=77):
     return [synth.make_inputs(w) for w in wls]
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
 def test_batch_matches_single_runs_and_oracle(prec):
     from paper_1507_07039_gb300 import panda
     nets = uneven_set()
@@ -38,6 +41,33 @@ def test_batch_matches_single_runs_and_oracle(prec):
         o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, iters[k])
         gh.assert_parity({"W": got[k][0], "P": got[k][1], "C": got[k][2]}, o, prec, f"network {k}")
     assert hist0.size == iters[0]
+
+
+@pytest.mark.parametrize("prec", [1, 3])
+def test_batch_runs_in_pieces(prec):
+    """Forty fixed iterations split over several calls (the schedule trials
+    spread over them, then the captured graph) end where one call of forty
+    ends, bit for bit.  (Networks that stop early are covered above.)"""
+    from paper_1507_07039_gb300 import panda
+    nets = uneven_set(6, seed=91)
+    with panda.PandaBatch(nets, prec=prec) as one:
+        _, iters1, _ = one.run(0.1, 0.0, 40)
+        ref = [one.get(k) for k in range(len(one))]
+    with panda.PandaBatch(nets, prec=prec) as b:
+        done = np.zeros(len(nets), int)
+        for chunk in (1, 2, 1, 3, 33):
+            _, it, _ = b.run(0.1, 0.0, chunk)
+            done += np.asarray(it)
+        got = [b.get(k) for k in range(len(b))]
+        epi, trial_ms, tuned = b.schedule()
+    assert list(done) == list(iters1) == [40] * len(nets)
+    for k in range(len(nets)):
+        for a, g in zip(ref[k], got[k]):
+            assert np.array_equal(a, g), f"network {k} differs"
+    # the trials ran (one iteration each) and the fastest schedule is the one in use
+    assert tuned and all(t > 0 for t in trial_ms)
+    weights = [48, 96, 192, 384, 768]
+    assert epi == weights[int(np.argmin(trial_ms))]
 
 
 def test_batch_errors_name_the_network():
