@@ -454,6 +454,7 @@ def run_set(args, rank, world, local_rank):
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
         ck = clocks.stop() if clocks else None
+        sched = b.schedule()
     assert all(i == args.steps for i in iters)
     value = len(wls) * args.steps / sec
     if rank == 0:
@@ -466,7 +467,10 @@ def run_set(args, rank, world, local_rank):
             "config": {"workload": "set64", "networks": len(wls), "T": [w.T for w in wls][:8] + ["..."],
                        "step": "one iteration of every network", "timing": "host clock between device syncs",
                        "parallelism": "single GPU"},
-            "useful_tflops": flops * args.steps / sec / 1e12, "clocks": ck}), flush=True)
+            "useful_tflops": flops * args.steps / sec / 1e12, "clocks": ck,
+            "schedule": None if sched is None else {
+                "epilogue_weight": sched[0], "trial_phase2_ms": [round(t, 3) for t in sched[1]],
+                "candidates": [48, 96, 192, 384, 768]}}), flush=True)
 
 
 def main(argv=None):
