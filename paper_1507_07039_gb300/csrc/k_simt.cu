@@ -213,27 +213,56 @@ __global__ void __launch_bounds__(NT, 2) k_phase1(Dev d, int cur)
 }
 
 // Slot sums for 32 consecutive rows per block, 8 threads per row: thread
-// (g, x) adds slots g, g + 8, g + 16, ... of row x in FP64, then the 8 partial
-// sums are added in group order (a fixed order, so the result is deterministic).
+// (g, x) adds slots g, g + 8, g + 16, ... of row x, then the 8 partial sums
+// are added in FP64 in group order (a fixed order, so the result is
+// deterministic).  The per-thread sums are compensated FP32 (each addition's
+// rounding error recovered exactly by Knuth's TwoSum and carried along), about
+// as accurate as FP64 additions of the FP32 slots but on the FP32 pipe, which
+// on this GPU is far wider than the FP64 one.
 constexpr int RS_ROWS = 32, RS_GROUPS = 8;
+
+// s + x = s' + e exactly (round to nearest, no overflow): s' = fl(s + x)
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+}
 
 template <int NV>
 __device__ __forceinline__ void slot_sums(const float *const (&src)[NV], int nslot, int ld, int x, bool ok,
                                           double (&out)[NV], double (*sh)[RS_GROUPS][RS_ROWS])
 {
     const int lx = threadIdx.x & (RS_ROWS - 1), g = threadIdx.x / RS_ROWS;
-    double acc[NV];
+    float s[NV], c[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-        acc[v] = 0.0;
-    if (ok)
-        for (int b = g; b < nslot; b += RS_GROUPS)
+        s[v] = c[v] = 0.0f;
+    if (ok) {
+        // four slots' loads in flight at a time; the additions keep the order b = g, g + 8, ...
+        int b = g;
+        for (; b + 3 * RS_GROUPS < nslot; b += 4 * RS_GROUPS) {
+            float t[NV][4];
 #pragma unroll
             for (int v = 0; v < NV; ++v)
-                acc[v] += (double)src[v][(size_t)b * ld + x];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    t[v][u] = src[v][(size_t)(b + u * RS_GROUPS) * ld + x];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    two_sum_add(s[v], c[v], t[v][u]);
+        }
+        for (; b < nslot; b += RS_GROUPS)
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                two_sum_add(s[v], c[v], src[v][(size_t)b * ld + x]);
+    }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
-        sh[v][g][lx] = acc[v];
+        sh[v][g][lx] = (double)s[v] + (double)c[v];
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
