@@ -473,6 +473,68 @@ def run_set(args, rank, world, local_rank):
                 "candidates": [48, 96, 192, 384, 768]}}), flush=True)
 
 
+# The paper's Table I (seconds for the whole message-passing loop, one thread,
+# x86_64 MIT SuperCloud, 100 random W per size, P = C = I): context beside the
+# replica below, not a target.
+PAPER_TABLE1 = {125: (1.05, 0.50, 0.13), 250: (4.65, 0.62, 0.54), 500: (32.73, 2.82, 2.61),
+                1000: (241.51, 15.82, 15.06), 2000: (1954.5, 98.59, 95.04)}
+
+
+def run_table1(args, rank, world, local_rank):
+    """Replica of the paper's Table I sweep: N_e = N_a = N, identity P and C,
+    random W (density 0.05), the message-passing loop run to h < 1e-3 at
+    alpha = 0.1, timed around panda_run only (create excluded, as the paper
+    excludes input and output).  Per N: one network alone (host clock around
+    the run, device synchronised), a batch of --table-reps such networks run
+    together (per-network time = batch time / reps), and the FP64 oracle on
+    the host cores, timed on a sampled fraction of one iteration and scaled by
+    the iteration count."""
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_1507_07039_gb300 import panda
+    prec = prec_code(panda, args.prec)
+    threads = cpu_threads()
+    rows = []
+    for n in (125, 250, 500, 1000, 2000):
+        nets = [synth.make_inputs(synth.table1(n, r)) for r in range(args.table_reps)]
+        W0, P0, C0 = nets[0]
+        with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:  # warm the library and the graph
+            ctx.run(ALPHA, 0.0, 2)
+        with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            conv, iters, _ = ctx.run(ALPHA, 1e-3, 1000)
+            torch.cuda.synchronize()
+            single = time.perf_counter() - t0
+        with panda.PandaBatch(nets, prec=prec) as b:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, it_b, _ = b.run(ALPHA, 1e-3, 1000)
+            torch.cuda.synchronize()
+            batch = time.perf_counter() - t0
+        row = {"N": n, "iterations": int(iters), "converged": bool(conv), "gpu_s": single,
+               "gpu_s_per_network_in_set": batch / len(nets), "set_networks": len(nets),
+               "set_iterations_mean": float(np.mean(it_b)),
+               "paper_s": dict(zip(("C-code", "Octave", "MATLAB"), PAPER_TABLE1[n]))}
+        if rank == 0 and args.cpu_baseline:
+            frac = min(1.0, 64.0 / n)
+            spi = OracleSample(W0, P0, C0, threads).run(frac)
+            row["oracle_s"] = spi * iters
+            row["oracle_sample"] = f"fraction {frac:.3f} of one iteration, scaled by {iters} iterations"
+        rows.append(row)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "PANDA run-time of the message-passing loop (paper Table I replica)",
+            "value": rows[-1]["gpu_s"], "unit": "s (N = 2000, one network)", "n_gpus": world, "steps": None,
+            "warmup": 1, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.prec.replace("fp32", "f32"), "data": "synthetic",
+            "config": {"workload": "table1", "alpha": ALPHA, "tol": 1e-3, "P, C": "identity",
+                       "W": "Bernoulli(0.05), normalised", "oracle_cores": threads,
+                       "paper_hardware": "MIT SuperCloud x86_64, one thread (C-code g++ -O3, Octave 3.8.2, "
+                                         "MATLAB R2014a)"},
+            "table": rows}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,11 +548,12 @@ def main(argv=None):
     ap.add_argument("--no-compare", dest="compare", action="store_false")
     ap.add_argument("--cpu-frac", type=float, default=0.1)
     ap.add_argument("--ref-frac", type=float, default=0.02)
+    ap.add_argument("--table-reps", type=int, default=16, help="networks per size in --workload table1")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     rank, world, local_rank = dist_env()
-    wl = synth.get(args.workload) if args.workload != "set64" else None
+    wl = synth.get(args.workload) if args.workload not in ("set64", "table1") else None
     if args.impl == "reference":
         run_reference(args, wl, rank, world)
         return
@@ -499,6 +562,9 @@ def main(argv=None):
         args.prec = "bf16x3" if panda.tensor_path_available() else "fp32"
     if args.workload == "set64":
         run_set(args, rank, world, local_rank)
+        return
+    if args.workload == "table1":
+        run_table1(args, rank, world, local_rank)
         return
     run_ours(args, wl, rank, world, local_rank)
 

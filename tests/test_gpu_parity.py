@@ -83,9 +83,10 @@ def test_other_diagonal_rules(orc, diag):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_identity_priors(orc, prec):
-    """The paper's Table I shape: P = C = I, random W."""
-    W0, P0, C0 = gh.inputs(synth.table1(125))
+@pytest.mark.parametrize("n", [125, 500])
+def test_identity_priors(orc, prec, n):
+    """The paper's Table I shape: P = C = I, random W (two of its sizes)."""
+    W0, P0, C0 = gh.inputs(synth.table1(n))
     o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 10)
     g = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 10)
     gh.assert_parity(g, o, prec, "identity priors")
