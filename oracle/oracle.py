@@ -59,6 +59,7 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "oracle_tanimoto": (d, [pd, l, pd, l, l]),
         "oracle_zscore": (i, [pd, l]),
         "oracle_normalize": (i, [i, i, pd, pd, pd]),
+        "oracle_pearson": (i, [i, i, pd, pd]),
         "oracle_responsibility": (d, [i, i, pd, pd, i, i]),
         "oracle_availability": (d, [i, i, pd, pd, i, i]),
         "oracle_w_entry": (d, [i, i, pd, pd, pd, d, i, i]),
@@ -127,6 +128,16 @@ class Oracle:
         if rc:
             raise ValueError(f"oracle_zscore failed ({rc})")
         return a
+
+    def pearson(self, X):
+        """Sec. II-A: the G x G Pearson correlation of the rows of X (G x N)."""
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        G, N = X.shape
+        C = np.empty((G, G), np.float64)
+        rc = self.lib.oracle_pearson(G, N, _p(X), _p(C))
+        if rc:
+            raise ValueError(f"oracle_pearson failed ({rc})")
+        return C
 
     def normalize(self, W, P, C):
         W, P, C = _f64(W).copy(), _f64(P).copy(), _f64(C).copy()

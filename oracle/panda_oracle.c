@@ -83,6 +83,56 @@ int oracle_zscore(double *a, long n)
     return 0;
 }
 
+int oracle_pearson(int G, int N, const double *X, double *C)
+{
+    if (G <= 0 || N <= 0 || !X || !C)
+        return -1;
+    double *mean = (double *)malloc(sizeof(double) * (size_t)G);
+    double *ss = (double *)malloc(sizeof(double) * (size_t)G);
+    if (!mean || !ss) {
+        free(mean);
+        free(ss);
+        return -1;
+    }
+    int degenerate = 0;
+    for (int g = 0; g < G; ++g) {
+        const double *x = X + (long)g * N;
+        double m = 0.0;
+        for (int k = 0; k < N; ++k)
+            m += x[k];
+        m /= (double)N;
+        double q = 0.0;
+        for (int k = 0; k < N; ++k)
+            q += (x[k] - m) * (x[k] - m);
+        mean[g] = m;
+        ss[g] = q;
+        if (!(q > 0.0))
+            degenerate = 1;
+    }
+    if (degenerate) {
+        free(mean);
+        free(ss);
+        return -6;
+    }
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int g = 0; g < G; ++g) {
+        const double *x = X + (long)g * N;
+        C[(long)g * G + g] = 1.0;
+        for (int h = g + 1; h < G; ++h) {
+            const double *y = X + (long)h * N;
+            double s = 0.0;
+            for (int k = 0; k < N; ++k)
+                s += (x[k] - mean[g]) * (y[k] - mean[h]);
+            const double r = s / sqrt(ss[g] * ss[h]);
+            C[(long)g * G + h] = r;
+            C[(long)h * G + g] = r;
+        }
+    }
+    free(mean);
+    free(ss);
+    return 0;
+}
+
 int oracle_normalize(int T, int G, double *W, double *P, double *C)
 {
     if (T <= 0 || G <= 0 || !W || !P || !C)

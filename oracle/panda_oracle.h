@@ -26,7 +26,8 @@
  * Parity status: every function here is pinned by the CPU tests (closed forms
  * of the similarity, the matrix form of Eq. 9, alpha = 0 and alpha = 1 cases,
  * identity-prior closed forms, a hand-worked 2 x 3 example, symmetry and
- * permutation equivariance).  Multi-iteration trajectories beyond those pins
+ * permutation equivariance; the Pearson initialisation against a library
+ * correlation, a worked 3 x 3 case, affine invariance and sign flips).  Multi-iteration trajectories beyond those pins
  * rest on the same per-step functions; the paper prints no worked trajectory.
  */
 #ifndef PANDA_ORACLE_H
@@ -37,6 +38,15 @@ extern "C" {
 #endif
 
 enum { ORACLE_DIAG_D1 = 0, ORACLE_DIAG_D0 = 1, ORACLE_DIAG_D2 = 2 };
+
+/* The initial co-regulation network (Sec. II-A): Pearson correlation between
+ * pairs of genes across all samples.  X is the G x N expression matrix
+ * (row-major, gene g's samples in X[g*N .. g*N + N-1]); C (G x G, row-major,
+ * full) receives r_gh = s_gh / sqrt(s_gg s_hh), s_gh = sum_k (x_gk - m_g)(x_hk - m_h)
+ * with m_g the mean of row g, and r_gg = 1.  Two passes in FP64 (means, then
+ * centred sums).  Returns 0; -1 for bad arguments; -6 when a row has zero
+ * variance (its correlations are undefined). */
+int oracle_pearson(int G, int N, const double *X, double *C);
 
 /* Eq. 1, in the three-sum form of Eq. 8: x.y / sqrt(|x|^2 + |y|^2 - |x.y|).
  * x and y are strided FP64 vectors of length n.  Both-zero vectors give 0. */

@@ -311,7 +311,43 @@ def pin_h_and_stop_rule(orc):
     assert n3 == 2, "h == tol continues"
 
 
+def pin_pearson(orc):
+    """Sec. II-A: the initial co-regulation network is the Pearson correlation
+    of the genes' expression across samples."""
+    rng = np.random.default_rng(61)
+    # a library routine of the same definition
+    for G, N in ((7, 13), (40, 25)):
+        X = rng.standard_normal((G, N)) * rng.uniform(0.5, 3.0, (G, 1)) + rng.uniform(-2, 2, (G, 1))
+        _close(orc.pearson(X), np.corrcoef(X), 1e-12, "numpy corrcoef")
+    # a worked case: rows 1 and 2 are affine images (r = 1), row 3 reversed (r = -1)
+    X = np.array([[1.0, 2.0, 3.0], [2.0, 4.0, 6.0], [3.0, 2.0, 1.0]])
+    _close(orc.pearson(X), np.array([[1, 1, -1], [1, 1, -1], [-1, -1, 1]], float), 1e-15, "hand 3 x 3")
+    # invariance under a positive scale and shift of a row; a negated row flips its sign
+    X = rng.standard_normal((9, 30))
+    C = orc.pearson(X)
+    Y = X.copy()
+    Y[4] = 7.5 * Y[4] - 3.0
+    _close(orc.pearson(Y), C, 1e-13, "affine invariance")
+    Y = X.copy()
+    Y[2] = -Y[2]
+    D = C.copy()
+    D[2, :] *= -1
+    D[:, 2] *= -1
+    _close(orc.pearson(Y), D, 1e-13, "negated row")
+    # symmetric, unit diagonal, |r| <= 1 (Cauchy-Schwarz)
+    assert np.array_equal(C, C.T) and np.all(np.diag(C) == 1.0) and np.all(np.abs(C) <= 1.0 + 1e-15)
+    # a constant gene has no correlation
+    X[5] = 2.0
+    try:
+        orc.pearson(X)
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("zero-variance row accepted")
+
+
 PINS = [
+    pin_pearson,
     pin_tanimoto_closed_forms,
     pin_tanimoto_properties,
     pin_zscore,

@@ -40,6 +40,9 @@ MUTANTS = {
     "h_not_mean": ("*h = s / ((double)T * (double)G);", "*h = s / ((double)T);"),
     "zscore_sample_std": ("double sd = sqrt(ss / (double)n);", "double sd = sqrt(ss / (double)(n - 1));"),
     "stop_not_strict": ("if (h < tol) {", "if (h <= tol) {"),
+    "pearson_uncentred": ("s += (x[k] - mean[g]) * (y[k] - mean[h]);", "s += x[k] * y[k];"),
+    "pearson_one_norm_twice": ("const double r = s / sqrt(ss[g] * ss[h]);", "const double r = s / ss[g];"),
+    "pearson_mean_off_by_one": ("        m /= (double)N;", "        m /= (double)(N - 1);"),
 }
 
 
