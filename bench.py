@@ -322,6 +322,27 @@ def time_e2e(panda, torch, W0, P0, C0, prec, steps):
     return t1 - t0, sum(x.nbytes for x in pin) / steps, sum(x.nbytes for x in outs) / steps
 
 
+def time_e2e_expression(panda, torch, wl, prec, steps):
+    """As time_e2e, starting from the expression data instead of C0: the
+    co-regulation prior is computed on the GPU (Sec. II-A), so the host sends
+    W0, P0 and the G x N expression matrix."""
+    W0, P0, X = synth.make_expression(wl)
+    pin = [torch.empty(x.shape, dtype=torch.float32, pin_memory=True).numpy() for x in (W0, P0, X)]
+    for dst, src in zip(pin, (W0, P0, X)):
+        np.copyto(dst, src)
+    T, G = W0.shape
+    outs = [torch.empty(s, dtype=torch.float32, pin_memory=True).numpy() for s in ((T, G), (T, T), (G, G))]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx = panda.PandaContext.from_expression(*pin, prec=prec)
+    t1 = time.perf_counter()
+    ctx.run(ALPHA, 0.0, steps)
+    panda.panda_get_into(ctx.h, *outs)
+    t2 = time.perf_counter()
+    ctx.close()
+    return t2 - t0, t1 - t0, sum(x.nbytes for x in pin) / steps, sum(x.nbytes for x in outs) / steps
+
+
 def run_ours(args, wl, rank, world, local_rank):
     import torch
     torch.cuda.set_device(local_rank)
@@ -386,6 +407,14 @@ def run_ours(args, wl, rank, world, local_rank):
                "unit": "iterations/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                "note": "create from pinned host buffers (H2D + validation + Z-score), the iterations, "
                        "read-back of W, P, C (D2H); per-step bytes = totals / steps"}
+        if wl.n_samples > 0:  # the same from expression data: C0 computed on the GPU (Pearson, Sec. II-A)
+            sec2, create2, bi2, bo2 = time_e2e_expression(panda, torch, wl, prec, args.steps)
+            sec2 = max_over_ranks(sec2, world, torch.device("cuda", local_rank))
+            e2e["from_expression"] = {
+                "value": world * args.steps / sec2, "unit": "iterations/s", "h2d_bytes_per_step": bi2,
+                "d2h_bytes_per_step": bo2, "create_s": create2,
+                "note": "panda_create_from_expression from pinned W0, P0 and the expression matrix "
+                        "(%d x %d), the iterations, read-back of W, P, C" % (wl.G, wl.n_samples)}
 
     cpu = None
     if rank == 0 and args.cpu_baseline:

@@ -198,6 +198,75 @@ __global__ void k_symmetrize(float *X, int n, int ld)
 
 }  // namespace
 
+namespace {
+
+// Pearson initialisation (Sec. II-A), first step: row g of the expression
+// matrix X (G x N, row-major) becomes z_g = (x_g - m_g) / |x_g - m_g|, so that
+// z_g . z_h is the correlation of genes g and h.  One warp per row; mean and
+// centred norm in FP64 (two passes, fixed lane order); z stored as a BF16
+// split (hi = bf16(z), lo = bf16(z - hi)) in Zh, Zl ([G][Kp], the padding left
+// zero by the caller).  flags[0] |= 1 on a non-finite sample, |= 2 on a row of
+// zero variance.
+__global__ void k_standardize_rows(const float *__restrict__ X, int G, int N, __nv_bfloat16 *__restrict__ Zh,
+                                   __nv_bfloat16 *__restrict__ Zl, int Kp, int *flags)
+{
+    const int g = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (g >= G)
+        return;
+    const float *x = X + (size_t)g * N;
+    double s = 0.0;
+    bool finite = true;
+    for (int k = lane; k < N; k += 32) {
+        finite = finite && isfinite(x[k]);
+        s += (double)x[k];
+    }
+    for (int off = 16; off >= 1; off >>= 1)
+        s += __shfl_xor_sync(0xffffffffu, s, off);
+    const double m = s / (double)N;
+    double q = 0.0;
+    for (int k = lane; k < N; k += 32) {
+        const double d = (double)x[k] - m;
+        q += d * d;
+    }
+    for (int off = 16; off >= 1; off >>= 1)
+        q += __shfl_xor_sync(0xffffffffu, q, off);
+    const unsigned bad = __ballot_sync(0xffffffffu, !finite);
+    if (lane == 0 && (bad || !(q > 0.0)))
+        atomicOr(flags, (bad ? 1 : 0) | (q > 0.0 ? 0 : 2));
+    if (bad || !(q > 0.0))
+        return;
+    const double inv = 1.0 / sqrt(q);
+    for (int k = lane; k < N; k += 32) {
+        const float z = (float)(((double)x[k] - m) * inv);
+        const __nv_bfloat16 hi = __float2bfloat16_rn(z);
+        Zh[(size_t)g * Kp + k] = hi;
+        Zl[(size_t)g * Kp + k] = __float2bfloat16_rn(z - __bfloat162float(hi));
+    }
+}
+
+// X_ii = 1 for i < n (a correlation matrix's diagonal)
+__global__ void k_unit_diag(float *X, int n, int ld)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n)
+        X[(size_t)i * ld + i] = 1.0f;
+}
+
+}  // namespace
+
+cudaError_t launch_standardize_rows(const float *X, int G, int N, __nv_bfloat16 *Zh, __nv_bfloat16 *Zl, int Kp,
+                                    int *flags, cudaStream_t s)
+{
+    k_standardize_rows<<<ceil_div(G, 8), 256, 0, s>>>(X, G, N, Zh, Zl, Kp, flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unit_diag(float *X, int n, int ld, cudaStream_t s)
+{
+    k_unit_diag<<<ceil_div(n, 256), 256, 0, s>>>(X, n, ld);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_symmetrize(float *X, int n, int ld, cudaStream_t s)
 {
     dim3 grid(ceil_div(n, 32), ceil_div(n, 32)), block(32, 8);

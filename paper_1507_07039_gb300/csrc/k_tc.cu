@@ -300,9 +300,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// Self-test of CTA pairs: D = A . B^T over 256 x 256 tiles, one pair of CTAs
-// per tile (cluster of 2 along x); CTA r loads A rows m0 + 128 r and B rows
-// n0 + 128 r and receives D rows m0 + 128 r .. + 127, all 256 columns.
+// D = A . B^T on CTA pairs over 256 x 256 tiles, one pair of CTAs per tile
+// (cluster of 2 along x); CTA r loads A rows m0 + 128 r and B rows n0 + 128 r
+// and receives D rows m0 + 128 r .. + 127, all 256 columns.  It serves the
+// Gram of the standardised expression (Pearson initialisation) and the
+// self-tests of the pair pipeline (MN-major B, E4M3 operands).
 // ---------------------------------------------------------------------------
 constexpr int PAIR_N = 256, PAIR_ST = 3;
 constexpr uint32_t PAIR_STAGE = 4 * A_BYTES;  // per CTA: A hi, A lo, B hi, B lo (128 rows each)
@@ -315,7 +317,7 @@ struct SyncPair {
 };
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
-    k_tc_selftest_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl, int bmn, int fp8)
+    k_tc_gemm_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl, int bmn, int fp8)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
@@ -1440,7 +1442,7 @@ cudaError_t set_smem_limits()
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
     if ((e = cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_tc_selftest_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((e = cudaFuncSetAttribute(k_tc_gemm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)pair_smem())))
         return e;
     done = true;
@@ -1691,6 +1693,20 @@ void tc_set_destroy(TcSet *t)
     delete t;
 }
 
+cudaError_t tc_gram(const __nv_bfloat16 *Zh, const __nv_bfloat16 *Zl, int Gp, int Kp, float *C, Ctl *ctl,
+                    cudaStream_t s)
+{
+    cudaError_t e = set_smem_limits();
+    if (e)
+        return e;
+    GemmMaps maps;
+    if ((e = make_map(&maps.Ah, Zh, Gp, Kp, 128)) || (e = make_map(&maps.Al, Zl, Gp, Kp, 128)) ||
+        (e = make_map(&maps.Bh, Zh, Gp, Kp, 128)) || (e = make_map(&maps.Bl, Zl, Gp, Kp, 128)))
+        return e;
+    k_tc_gemm_pair<<<dim3(Gp / 128, Gp / PAIR_N), THREADS, pair_smem(), s>>>(maps, Kp, Gp, C, ctl, 0, 0);
+    return cudaGetLastError();
+}
+
 // D = A . B^T on the tensor-core pipeline (self-test support)
 cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms,
                              int pair, int stall_kb, int *status)
@@ -1742,7 +1758,7 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
         TRY(cudaGetLastError());
         TRY(make_map8(&maps.Ah, Ah, Mp, Kp, 128));
         TRY(make_map8(&maps.Bh, Bh, Np, Kp, 128));
-        k_tc_selftest_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl, 0, 1);
+        k_tc_gemm_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl, 0, 1);
         TRY(cudaGetLastError());
         TRY(cudaDeviceSynchronize());
         Ctl h;
@@ -1770,7 +1786,7 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     }
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
     if (pair)
-        k_tc_selftest_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl,
+        k_tc_gemm_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl,
                                                                                     pair == 2, 0);
     else
         k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl, stall_kb);

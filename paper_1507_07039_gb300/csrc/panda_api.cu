@@ -191,10 +191,12 @@ int push_ctl(panda_ctx *c)
 }
 
 // Copy a rows x cols row-major matrix (host or device) into a padded buffer.
-int upload(panda_ctx *c, float *dst, int ld, const float *src, int rows, int cols)
+// src: host or device (cudaMemcpyDefault), row stride src_ld (0: cols)
+int upload(panda_ctx *c, float *dst, int ld, const float *src, int rows, int cols, int src_ld = 0)
 {
-    CU(cudaMemcpy2DAsync(dst, (size_t)ld * sizeof(float), src, (size_t)cols * sizeof(float),
-                         (size_t)cols * sizeof(float), rows, cudaMemcpyDefault, c->stream));
+    const size_t spitch = (size_t)(src_ld > 0 ? src_ld : cols) * sizeof(float);
+    CU(cudaMemcpy2DAsync(dst, (size_t)ld * sizeof(float), src, spitch, (size_t)cols * sizeof(float), rows,
+                         cudaMemcpyDefault, c->stream));
     return 0;
 }
 
@@ -452,8 +454,9 @@ void free_all(panda_ctx *c)
         cudaStreamDestroy(c->stream);
 }
 
+// C0's row stride is ldc (0: G); the sources may be host or device memory.
 int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P0, const float *C0,
-                  const panda_opts *o, void *stream, bool device_ptrs)
+                  const panda_opts *o, void *stream, bool device_ptrs, int ldc = 0)
 {
     if (!out)
         return set_err(nullptr, PANDA_EINVAL, "out is NULL");
@@ -523,7 +526,7 @@ int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P
     if ((rc = plan_memory(c)))
         return fail(rc);
     if ((rc = upload(c, c->d.W[0], c->Gp, W0, T, G)) || (rc = upload(c, c->d.Poff, c->Tp, P0, T, T)) ||
-        (rc = upload(c, c->d.Coff, c->Gp, C0, G, G)))
+        (rc = upload(c, c->d.Coff, c->Gp, C0, G, G, ldc)))
         return fail(rc);
     if ((rc = validate(c)))
         return fail(rc);
@@ -580,6 +583,83 @@ int panda_create_device(panda_ctx **out, int T, int G, const float *dW0, const f
                         const float *dC0, const panda_opts *o, void *stream)
 {
     return create_common(out, T, G, dW0, dP0, dC0, o, stream, true);
+}
+
+int panda_create_from_expression(panda_ctx **out, int T, int G, int N, const float *W0, const float *P0,
+                                 const float *X, const panda_opts *o)
+{
+    if (!out)
+        return set_err(nullptr, PANDA_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (T <= 0 || G <= 0 || N <= 0 || !W0 || !X)
+        return set_err(nullptr, PANDA_EINVAL, "T, G, N must be positive; W0 and X must not be NULL");
+    if (G > 46000 || T > 46000)
+        return set_err(nullptr, PANDA_EINVAL, "T and G must be at most 46000");
+    if (!tc_supported())
+        return set_err(nullptr, PANDA_EUNSUPPORTED, "the GPU Pearson initialisation needs an sm_103 device");
+    const int Gp = round_up(G, 2 * TILE), Kp = round_up(N, 64);
+    cudaStream_t s = nullptr;
+    float *dX = nullptr, *dC = nullptr;
+    __nv_bfloat16 *Zh = nullptr, *Zl = nullptr;
+    int *flags = nullptr;
+    Ctl *ctl = nullptr;
+    std::vector<float> eye;
+    auto cleanup = [&]() {
+        if (s)
+            cudaStreamSynchronize(s);
+        cudaFree(dX); cudaFree(dC); cudaFree(Zh); cudaFree(Zl); cudaFree(flags); cudaFree(ctl);
+        if (s)
+            cudaStreamDestroy(s);
+    };
+    cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) ||
+        (e = cudaMalloc(&dX, sizeof(float) * (size_t)G * N)) ||
+        (e = cudaMalloc(&dC, sizeof(float) * (size_t)Gp * Gp)) ||
+        (e = cudaMalloc(&Zh, sizeof(__nv_bfloat16) * (size_t)Gp * Kp)) ||
+        (e = cudaMalloc(&Zl, sizeof(__nv_bfloat16) * (size_t)Gp * Kp)) || (e = cudaMalloc(&flags, sizeof(int))) ||
+        (e = cudaMalloc(&ctl, sizeof(Ctl)))) {
+        const int code = e == cudaErrorMemoryAllocation ? PANDA_ENOMEM : PANDA_ECUDA;
+        cleanup();
+        return set_err(nullptr, code, std::string("panda_create_from_expression: ") + cudaGetErrorString(e));
+    }
+    int hflags = 0;
+    Ctl hctl{};
+    if ((e = cudaMemsetAsync(Zh, 0, sizeof(__nv_bfloat16) * (size_t)Gp * Kp, s)) ||
+        (e = cudaMemsetAsync(Zl, 0, sizeof(__nv_bfloat16) * (size_t)Gp * Kp, s)) ||
+        (e = cudaMemsetAsync(flags, 0, sizeof(int), s)) || (e = cudaMemsetAsync(ctl, 0, sizeof(Ctl), s)) ||
+        (e = cudaMemcpyAsync(dX, X, sizeof(float) * (size_t)G * N, cudaMemcpyDefault, s)) ||
+        (e = launch_standardize_rows(dX, G, N, Zh, Zl, Kp, flags, s)) ||
+        (e = cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s))) {
+        cleanup();
+        return set_err(nullptr, PANDA_ECUDA, std::string("panda_create_from_expression: ") + cudaGetErrorString(e));
+    }
+    if (hflags) {
+        cleanup();
+        return set_err(nullptr, hflags & 1 ? PANDA_ENONFINITE : PANDA_EDEGENERATE,
+                       hflags & 1 ? "panda_create_from_expression: a sample is not finite"
+                                  : "panda_create_from_expression: a gene has zero variance across the samples");
+    }
+    // correlations: the Gram of the unit-norm centred rows, its upper triangle mirrored, unit diagonal
+    if ((e = tc_gram(Zh, Zl, Gp, Kp, dC, ctl, s)) || (e = launch_symmetrize(dC, G, Gp, s)) ||
+        (e = launch_unit_diag(dC, G, Gp, s)) ||
+        (e = cudaMemcpyAsync(&hctl, ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s)) || (e = cudaStreamSynchronize(s))) {
+        cleanup();
+        return set_err(nullptr, PANDA_ECUDA, std::string("panda_create_from_expression: ") + cudaGetErrorString(e));
+    }
+    if (hctl.status & ST_TIMEOUT) {
+        cleanup();
+        return set_err(nullptr, PANDA_ETIMEOUT, "panda_create_from_expression: a bounded device wait expired");
+    }
+    if (!P0) {  // no interaction data: the identity (Sec. II-A)
+        eye.assign((size_t)T * T, 0.0f);
+        for (int i = 0; i < T; ++i)
+            eye[(size_t)i * T + i] = 1.0f;
+        P0 = eye.data();
+    }
+    const int rc = create_common(out, T, G, W0, P0, dC, o, nullptr, false, Gp);
+    cleanup();
+    return rc;
 }
 
 int panda_step(panda_ctx *c, float alpha, double *h_out)

@@ -129,6 +129,11 @@ cudaError_t launch_diag_to_float(const double *d, float *df, int n, cudaStream_t
 cudaError_t launch_scan_nonfinite(const float *X, long long n, int *flag, cudaStream_t s);
 // X[r][c] = X[c][r] for r > c: the full matrix from its upper triangle
 cudaError_t launch_symmetrize(float *X, int n, int ld, cudaStream_t s);
+// Pearson initialisation (Sec. II-A): unit-norm centred rows of X (G x N) as a
+// BF16 split [G][Kp]; flags[0] |= 1 (non-finite) / 2 (zero variance)
+cudaError_t launch_standardize_rows(const float *X, int G, int N, __nv_bfloat16 *Zh, __nv_bfloat16 *Zl, int Kp,
+                                    int *flags, cudaStream_t s);
+cudaError_t launch_unit_diag(float *X, int n, int ld, cudaStream_t s);
 
 // Optional per-kernel timing: when ev is not NULL, ev[0] is recorded before the
 // first kernel of the iteration and ev[k + 1] after kernel k.
@@ -172,6 +177,12 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
 // Phase-2 schedules for TC_SET_CANDS epilogue weights are built; a tile's
 // result does not depend on which pair computes it, so any schedule gives the
 // same bits and the fastest can be picked by timing real iterations.
+// C (Gp x Gp, FP32, row stride Gp) = Z . Z^T with the three-term BF16 split of
+// Z ([Gp][Kp] hi and lo, Gp a multiple of 256, Kp of 64) on CTA pairs; a
+// timed-out wait sets ST_TIMEOUT in ctl (device memory).
+cudaError_t tc_gram(const __nv_bfloat16 *Zh, const __nv_bfloat16 *Zl, int Gp, int Kp, float *C, Ctl *ctl,
+                    cudaStream_t s);
+
 struct TcSet;
 constexpr int TC_SET_CANDS = 5;
 extern const int TC_SET_EPI[TC_SET_CANDS];

@@ -67,6 +67,7 @@ def _load() -> ctypes.CDLL:
         "panda_step_static": (i, [i, i, vp, vp, vp, f, i, i, pd, vp]),
         "panda_selftest_tc_gemm": (i, [i, i, i, vp, vp, vp, i]),
         "panda_selftest_timeout": (i, []),
+        "panda_create_from_expression": (i, [pvp, i, i, i, vp, vp, vp, popts]),
         "panda_batch_create": (i, [pvp, i, pi, pi, pvp, pvp, pvp, popts]),
         "panda_batch_run": (i, [vp, f, d, i, pi, pd]),
         "panda_batch_get": (i, [vp, i, vp, vp, vp]),
@@ -125,6 +126,19 @@ def panda_create(T, G, W0, P0, C0, opts: panda_opts | None = None):
     h = ctypes.c_void_p()
     _check(lib.panda_create(ctypes.byref(h), T, G, _ptr(W0), _ptr(P0), _ptr(C0),
                             ctypes.byref(opts) if opts is not None else None))
+    return h
+
+
+def panda_create_from_expression(W0, P0, X, opts: panda_opts | None = None):
+    """C0 from the expression matrix X (G x N) on the GPU (Pearson, Sec. II-A);
+    P0 may be None (identity).  Host numpy inputs; returns a context handle."""
+    T, G = np.shape(W0)
+    N = np.shape(X)[1]
+    W0, X = _host_f32(W0, (T, G)), _host_f32(X, (G, N))
+    P0 = None if P0 is None else _host_f32(P0, (T, T))
+    h = ctypes.c_void_p()
+    _check(lib.panda_create_from_expression(ctypes.byref(h), T, G, N, _ptr(W0), None if P0 is None else _ptr(P0),
+                                            _ptr(X), ctypes.byref(opts) if opts is not None else None))
     return h
 
 
@@ -303,6 +317,17 @@ class PandaContext:
             self.h = panda_create_device(T, G, W0, P0, C0, opts, stream)
         else:
             self.h = panda_create(T, G, W0, P0, C0, opts)
+
+    @classmethod
+    def from_expression(cls, W0, P0, X, prec=PANDA_FP32, diag=PANDA_DIAG_D1, normalize=True, t0=0,
+                        graph_iters=8):
+        """A context whose C0 is the Pearson correlation of X's rows, computed on the GPU."""
+        self = cls.__new__(cls)
+        self.T, self.G = np.shape(W0)
+        opts = default_opts(prec=prec, diag=diag, normalize=int(bool(normalize)), t0=t0,
+                            graph_iters=graph_iters)
+        self.h = panda_create_from_expression(W0, P0, X, opts)
+        return self
 
     def step(self, alpha=0.1) -> float:
         return panda_step(self.h, alpha)

@@ -84,12 +84,17 @@ def set_of_networks(count: int = 64, seed: int = BASE_SEED + 1000, t_range=(200,
             for k in range(count)]
 
 
-def _expression_correlation(rng: np.random.Generator, G: int, n: int, k: int,
-                            block: int = 2048) -> np.ndarray:
+def _expression(rng: np.random.Generator, G: int, n: int, k: int) -> np.ndarray:
+    """G genes x n samples: k latent N(0, 1) factors plus N(0, 0.5^2) noise."""
     L = rng.standard_normal((G, k))
     F = rng.standard_normal((k, n))
     E = rng.normal(0.0, 0.5, size=(G, n))
-    X = L @ F + E
+    return L @ F + E
+
+
+def _expression_correlation(rng: np.random.Generator, G: int, n: int, k: int,
+                            block: int = 2048) -> np.ndarray:
+    X = _expression(rng, G, n, k)
     X -= X.mean(axis=1, keepdims=True)
     X /= np.sqrt((X * X).sum(axis=1, keepdims=True))
     C = np.empty((G, G), dtype=np.float32)
@@ -115,6 +120,20 @@ def make_inputs(wl: Workload):
     np.fill_diagonal(P0, 1.0)
     C0 = _expression_correlation(rng, G, wl.n_samples, wl.n_factors)
     return W0, P0, C0
+
+
+def make_expression(wl: Workload):
+    """Return (W0, P0, X): the same W0 and P0 as make_inputs and the expression
+    matrix (G x n_samples, float32) whose gene correlations make_inputs' C0 is."""
+    assert not wl.identity_priors, "identity-prior workloads have no expression data"
+    rng = np.random.Generator(np.random.PCG64(wl.seed))
+    T, G = wl.T, wl.G
+    W0 = (rng.random((T, G)) < wl.w_density).astype(np.float32)
+    up = np.triu(rng.random((T, T)) < wl.p_density, 1)
+    P0 = (up | up.T).astype(np.float32)
+    np.fill_diagonal(P0, 1.0)
+    X = _expression(rng, G, wl.n_samples, wl.n_factors).astype(np.float32)
+    return W0, P0, X
 
 
 def gene_subsample(G: int, n: int, seed: int) -> np.ndarray:
