@@ -222,9 +222,10 @@ class OracleSample:
         rows_t = (self.cursor + np.arange(rT)) % self.T
         rows_g = (self.cursor + np.arange(rG)) % self.G
         self.cursor += rT
-        a = ALPHA
+        a = float(np.float32(ALPHA))  # the library takes alpha as FP32
         t0 = time.perf_counter()
-        self.orc.w_rows(self.W, self.P, self.C, a, rows_t)
+        self.w_rows = self.orc.w_rows(self.W, self.P, self.C, a, rows_t)
+        self.rows = rows_t
         t1 = time.perf_counter()
         self.orc.p_rows(self.W, self.P, a, rows_t)
         t2 = time.perf_counter()
@@ -417,6 +418,7 @@ def run_ours(args, wl, rank, world, local_rank):
                         "(%d x %d), the iterations, read-back of W, P, C" % (wl.G, wl.n_samples)}
 
     cpu = None
+    accuracy = None
     if rank == 0 and args.cpu_baseline:
         threads = cpu_threads()
         s = OracleSample(W0, P0, C0, threads)
@@ -427,6 +429,13 @@ def run_ours(args, wl, rank, world, local_rank):
                "sample": f"fraction {args.cpu_frac} of one iteration ({max(1, round(args.cpu_frac * T))} rows "
                          f"of W' and of P', {max(1, round(args.cpu_frac * G))} rows of C'), "
                          f"{el:.1f} s of CPU time, scaled to a full iteration"}
+        # the same rows of the first iteration's W' on the GPU, against the oracle's (the metric's gate)
+        with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:
+            ctx.step(ALPHA)
+            gW = ctx.get(want=(True, False, False))[0]
+        err = float(np.max(np.abs(gW[s.rows].astype(np.float64) - s.w_rows)))
+        accuracy = {"max_abs_dW_vs_fp64_oracle": err, "rows": int(len(s.rows)), "of": T, "iteration": 1,
+                    "gate": 1e-4, "within_gate": err <= 1e-4}
 
     launches = int(sum(k[2] for k in kstats))
     if rank == 0:
@@ -443,6 +452,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "useful_tflops": value / world * algorithmic_flops(T, G) / 1e12,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "accuracy": accuracy,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": ck,

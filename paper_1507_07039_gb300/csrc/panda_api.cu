@@ -5,6 +5,8 @@
 #include "panda.h"
 #include "panda_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -41,6 +43,12 @@ struct panda_ctx {
 namespace {
 
 thread_local std::string g_create_error = "no error";
+
+// An NVTX range over one API call, for timeline tools (no cost without one attached)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 // the modes that run on the tensor-core path (k_tc.cu)
 bool tensor_prec(int prec) { return prec == PANDA_BF16X3 || prec == PANDA_BF16X2 || prec == PANDA_FP8MIX; }
@@ -576,18 +584,21 @@ void panda_default_opts(panda_opts *o)
 int panda_create(panda_ctx **out, int T, int G, const float *W0, const float *P0, const float *C0,
                  const panda_opts *o)
 {
+    Range r("panda_create");
     return create_common(out, T, G, W0, P0, C0, o, nullptr, false);
 }
 
 int panda_create_device(panda_ctx **out, int T, int G, const float *dW0, const float *dP0,
                         const float *dC0, const panda_opts *o, void *stream)
 {
+    Range r("panda_create_device");
     return create_common(out, T, G, dW0, dP0, dC0, o, stream, true);
 }
 
 int panda_create_from_expression(panda_ctx **out, int T, int G, int N, const float *W0, const float *P0,
                                  const float *X, const panda_opts *o)
 {
+    Range range("panda_create_from_expression");
     if (!out)
         return set_err(nullptr, PANDA_EINVAL, "out is NULL");
     *out = nullptr;
@@ -664,6 +675,7 @@ int panda_create_from_expression(panda_ctx **out, int T, int G, int N, const flo
 
 int panda_step(panda_ctx *c, float alpha, double *h_out)
 {
+    Range r("panda_step");
     if (check_ctx(c))
         return PANDA_EINVAL;
     if (!(alpha >= 0.0f && alpha <= 1.0f))
@@ -679,6 +691,7 @@ int panda_step(panda_ctx *c, float alpha, double *h_out)
 
 int panda_run(panda_ctx *c, float alpha, double tol, int max_iter, int *iters_out, double *h_last)
 {
+    Range r("panda_run");
     if (check_ctx(c))
         return PANDA_EINVAL;
     if (!(alpha >= 0.0f && alpha <= 1.0f))
@@ -741,6 +754,7 @@ static int get_impl(panda_ctx *c, float *W, float *P, float *C)
 
 int panda_get(panda_ctx *c, float *W, float *P, float *C)
 {
+    Range r("panda_get");
     if (check_ctx(c))
         return PANDA_EINVAL;
     return get_impl(c, W, P, C);
@@ -1201,6 +1215,7 @@ int panda_batch_create(panda_batch **out, int n, const int *T, const int *G, con
 
 int panda_batch_run(panda_batch *b, float alpha, double tol, int max_iter, int *iters_out, double *h_last)
 {
+    Range r("panda_batch_run");
     if (!b)
         return PANDA_EINVAL;
     if (!(alpha >= 0.0f && alpha <= 1.0f) || !(tol >= 0.0) || max_iter < 0) {
