@@ -472,6 +472,7 @@ def run_set(args, rank, world, local_rank):
     value = network-iterations/s."""
     import torch
     torch.cuda.set_device(local_rank)
+    dist_init(world)
     from paper_1507_07039_gb300 import panda
     prec = prec_code(panda, args.prec)
     wls = synth.set_of_networks(64)
@@ -488,14 +489,17 @@ def run_set(args, rank, world, local_rank):
         if clocks:
             clocks.start()
             time.sleep(0.6)
+        barrier(world)
         t0 = time.perf_counter()
         conv, iters, _ = b.run(ALPHA, 0.0, args.steps)
         torch.cuda.synchronize()
         sec = time.perf_counter() - t0
+        barrier(world)
+        sec = max_over_ranks(sec, world, torch.device("cuda", local_rank))  # replicas: the slowest rank
         ck = clocks.stop() if clocks else None
         sched = b.schedule()
     assert all(i == args.steps for i in iters)
-    value = len(wls) * args.steps / sec
+    value = world * len(wls) * args.steps / sec  # the whole job: every rank iterates its own copy of the set
     if rank == 0:
         print(json.dumps({
             "metric": "PANDA network-iterations/s over a set of networks", "value": value,
@@ -505,11 +509,14 @@ def run_set(args, rank, world, local_rank):
             "warmup_iterations": warm,
             "config": {"workload": "set64", "networks": len(wls), "T": [w.T for w in wls][:8] + ["..."],
                        "step": "one iteration of every network", "timing": "host clock between device syncs",
-                       "parallelism": "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
             "useful_tflops": flops * args.steps / sec / 1e12, "clocks": ck,
             "schedule": None if sched is None else {
                 "epilogue_weight": sched[0], "trial_phase2_ms": [round(t, 3) for t in sched[1]],
                 "candidates": [48, 96, 192, 384, 768]}}), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 # The paper's Table I (seconds for the whole message-passing loop, one thread,
