@@ -14,18 +14,65 @@ namespace {
 constexpr int RED_BLOCKS = 1024;
 constexpr int RED_THREADS = 256;
 
-// flags[0] |= 1 on a non-finite entry; flags[1] |= 1 when X[i][j] != X[j][i].
-__global__ void k_check_finite_sym(const float *__restrict__ X, int rows, int cols, int ld,
-                                   int sym, int *flags)
+// flags[0] |= 1 on a non-finite entry (rows x cols, row stride ld): block b
+// reads rows b, b + gridDim.x, ... along the row.
+__global__ void k_check_finite(const float *__restrict__ X, int rows, int cols, int ld, int *flags)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= cols)
-        return;
-    for (int r = blockIdx.y; r < rows; r += gridDim.y) {
-        float v = X[(size_t)r * ld + c];
-        if (!isfinite(v))
+    int bad = 0;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x)
+        for (int c = threadIdx.x; c < cols; c += blockDim.x)
+            bad |= !isfinite(X[(size_t)r * ld + c]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0)
+        atomicOr(&flags[0], 1);
+}
+
+// A square n x n matrix as 32 x 32 blocks: each pair of mirror blocks (bi, bj)
+// and (bj, bi), bi <= bj, is read once, along rows, into shared memory, so the
+// whole matrix is read once and coalesced.  flags[0] |= 1 on a non-finite
+// entry, flags[1] |= 1 when X[i][j] != X[j][i].  Pairs are numbered column by
+// column of the upper triangle: pair t has bj = the largest j with
+// j(j+1)/2 <= t and bi = t - bj(bj+1)/2.  256 threads.
+__global__ void k_check_finite_sym(const float *__restrict__ X, int n, int ld, int npairs, int *flags)
+{
+    __shared__ float a[32][33], b[32][33];
+    __shared__ int pij[2];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    int bad = 0, asym = 0;
+    for (int t = blockIdx.x; t < npairs; t += gridDim.x) {
+        if (threadIdx.x == 0) {
+            // 8t + 1 < 2^24 for n <= 46000, so the FP32 square root is close; the loops correct it
+            int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+            while (j > 0 && (long long)j * (j + 1) / 2 > t)
+                --j;
+            while ((long long)(j + 1) * (j + 2) / 2 <= t)
+                ++j;
+            pij[0] = t - (int)((long long)j * (j + 1) / 2);
+            pij[1] = j;
+        }
+        __syncthreads();
+        const int i0 = pij[0] * 32, j0 = pij[1] * 32;
+#pragma unroll
+        for (int k = ty; k < 32; k += 8) {
+            const int ra = i0 + k, ca = j0 + tx, rb = j0 + k, cb = i0 + tx;
+            a[k][tx] = (ra < n && ca < n) ? X[(size_t)ra * ld + ca] : 0.0f;
+            b[k][tx] = (rb < n && cb < n) ? X[(size_t)rb * ld + cb] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = ty; k < 32; k += 8) {
+            // a[k][tx] = X[i0 + k][j0 + tx], its mirror X[j0 + tx][i0 + k] = b[tx][k]
+            const float v = a[k][tx];
+            bad |= !isfinite(v) | !isfinite(b[k][tx]);
+            asym |= (i0 + k < n && j0 + tx < n && v != b[tx][k]);
+        }
+        __syncthreads();
+    }
+    bad = __syncthreads_or(bad);
+    asym = __syncthreads_or(asym);
+    if (threadIdx.x == 0) {
+        if (bad)
             atomicOr(&flags[0], 1);
-        if (sym && c > r && v != X[(size_t)c * ld + r])
+        if (asym)
             atomicOr(&flags[1], 1);
     }
 }
@@ -45,29 +92,85 @@ __device__ double block_sum_fixed(double v, double *sh)
     return r;
 }
 
-// mode 0: sum of x; mode 1: sum of (x - mean)^2 with mean = stats[0]
-__global__ void k_stats_partial(const float *__restrict__ X, int rows, int cols, int ld, int mode,
-                                const double *stats, double *partials)
+// The FP32 pairs the element kernels use, stored after the FP64 statistics:
+// stats[0] = mean, stats[1] = population std, then as floats (16-byte
+// aligned) mean = mh + ml and 1 / std = rh + rl, each to about 2^-48.
+__device__ __forceinline__ float4 *stats_pairs(double *stats) { return reinterpret_cast<float4 *>(stats + 2); }
+__device__ __forceinline__ float4 stats_pairs(const double *stats)
+{
+    return *reinterpret_cast<const float4 *>(stats + 2);
+}
+
+// x - (mh + ml) = s + t: s = fl(x - mh) and t its rounding error minus ml
+__device__ __forceinline__ void centre(float x, float mh, float ml, float &s, float &t)
+{
+    float e;
+    two_sum(x, -mh, s, e);
+    t = __fsub_rn(e, ml);
+}
+
+// Adds the terms of one element to a compensated pair: mode 0 adds x; mode 1
+// adds (x - mean)^2 = (s + t)^2 = p + (pe + 2 s t + t^2), with s^2 = p + pe
+// exact.
+template <int MODE>
+__device__ __forceinline__ void stats_term(float x, float mh, float ml, float &acc, float &cmp)
+{
+    if (MODE == 0) {
+        two_sum_add(acc, cmp, x);
+    } else {
+        float s, t, p, pe;
+        centre(x, mh, ml, s, t);
+        two_prod(s, s, p, pe);
+        two_sum_add(acc, cmp, p);
+        cmp = __fadd_rn(cmp, __fmaf_rn(t, t, __fmaf_rn(__fmul_rn(2.0f, s), t, pe)));
+    }
+}
+
+// Partial sums for the Z-score in a fixed order.  Block b takes rows b,
+// b + gridDim.x, ...; thread x takes the 4-wide column groups x, x + 256, ...
+// of each (rows start 16-byte aligned), then the ragged columns.  A thread's
+// terms within one row go into a compensated FP32 pair (TwoSum), the pair
+// into the thread's FP64 total at the row's end, and the block's totals
+// through a fixed tree.  Mode 0: sum of x.  Mode 1: sum of (x - mean)^2,
+// mean from stats (the difference kept as an FP32 pair, its square from
+// two_prod).  About as accurate as FP64 sums of the FP32 entries, on the FP32
+// pipe.
+template <int MODE>
+__global__ void k_stats_partial(const float *__restrict__ X, int rows, int cols, int ld, const double *stats,
+                                double *partials)
 {
     __shared__ double sh[RED_THREADS];
-    double mean = mode ? stats[0] : 0.0;
-    double acc = 0.0;
-    for (int r = blockIdx.x; r < rows; r += gridDim.x)
-        for (int c = threadIdx.x; c < cols; c += blockDim.x) {
-            double v = (double)X[(size_t)r * ld + c];
-            if (mode) {
-                double d = v - mean;
-                acc += d * d;
-            } else {
-                acc += v;
-            }
+    float mh = 0.0f, ml = 0.0f;
+    if (MODE == 1) {
+        const float4 q = stats_pairs(stats);
+        mh = q.x;
+        ml = q.y;
+    }
+    const int c4n = cols >> 2;
+    double tot = 0.0;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float *x = X + (size_t)r * ld;
+        const float4 *x4 = reinterpret_cast<const float4 *>(x);
+        float acc = 0.0f, cmp = 0.0f;
+#pragma unroll 2
+        for (int c = threadIdx.x; c < c4n; c += RED_THREADS) {
+            const float4 v = __ldcs(x4 + c);
+            stats_term<MODE>(v.x, mh, ml, acc, cmp);
+            stats_term<MODE>(v.y, mh, ml, acc, cmp);
+            stats_term<MODE>(v.z, mh, ml, acc, cmp);
+            stats_term<MODE>(v.w, mh, ml, acc, cmp);
         }
-    double s = block_sum_fixed(acc, sh);
+        for (int c = (c4n << 2) + threadIdx.x; c < cols; c += RED_THREADS)
+            stats_term<MODE>(x[c], mh, ml, acc, cmp);
+        tot += (double)acc + (double)cmp;
+    }
+    double s = block_sum_fixed(tot, sh);
     if (threadIdx.x == 0)
         partials[blockIdx.x] = s;
 }
 
-// stats[0] = mean (mode 0) or stats[1] = population std (mode 1)
+// Mode 0: stats[0] = mean and its FP32 pair.  Mode 1: stats[1] = population
+// std and the FP32 pair of its reciprocal (zero when std is not positive).
 __global__ void k_stats_final(const double *partials, int n, double count, int mode, double *stats)
 {
     __shared__ double sh[RED_THREADS];
@@ -76,22 +179,59 @@ __global__ void k_stats_final(const double *partials, int n, double count, int m
         acc += partials[i];
     double s = block_sum_fixed(acc, sh);
     if (threadIdx.x == 0) {
-        if (mode == 0)
-            stats[0] = s / count;
-        else
-            stats[1] = sqrt(s / count);
+        float4 *q = stats_pairs(stats);
+        if (mode == 0) {
+            const double m = s / count;
+            stats[0] = m;
+            const float mh = (float)m;
+            q->x = mh;
+            q->y = (float)(m - (double)mh);
+        } else {
+            const double sd = sqrt(s / count);
+            stats[1] = sd;
+            const double r = sd > 0.0 ? 1.0 / sd : 0.0;
+            const float rh = (float)r;
+            q->z = rh;
+            q->w = (float)(r - (double)rh);
+        }
     }
 }
 
+// z = (x - mean) / std (Section II-A, NormalizeNetwork) from the FP32 pairs:
+// (s + t) (rh + rl) = s rh + (its exact rounding error + s rl + t rh), the
+// terms left out being below 2^-44 of z; the final FP32 addition rounds that
+// sum once.  The FP32 result therefore equals the correctly rounded quotient
+// except when that lies within about 2^-44 relative of a rounding midpoint.
+__device__ __forceinline__ float zscore_one(float x, float4 q)
+{
+    float s, t, p, pe;
+    centre(x, q.x, q.y, s, t);
+    two_prod(s, q.z, p, pe);
+    return __fadd_rn(p, __fmaf_rn(t, q.z, __fmaf_rn(s, q.w, pe)));
+}
+
+// Block b takes rows b, b + gridDim.x, ...; 4-wide column groups, then the
+// ragged columns.
 __global__ void k_apply_zscore(float *X, int rows, int cols, int ld, const double *stats)
 {
-    int c = blockIdx.x * blockDim.x + threadIdx.x;
-    double sd = stats[1];
-    if (c >= cols || !(sd > 0.0))
+    if (!(stats[1] > 0.0))
         return;
-    for (int r = blockIdx.y; r < rows; r += gridDim.y) {
-        size_t o = (size_t)r * ld + c;
-        X[o] = (float)(((double)X[o] - stats[0]) / sd);
+    const float4 q = stats_pairs(stats);
+    const int c4n = cols >> 2;
+    for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+        float *x = X + (size_t)r * ld;
+        float4 *x4 = reinterpret_cast<float4 *>(x);
+#pragma unroll 2
+        for (int c = threadIdx.x; c < c4n; c += blockDim.x) {
+            float4 v = x4[c];
+            v.x = zscore_one(v.x, q);
+            v.y = zscore_one(v.y, q);
+            v.z = zscore_one(v.z, q);
+            v.w = zscore_one(v.w, q);
+            x4[c] = v;
+        }
+        for (int c = (c4n << 2) + threadIdx.x; c < cols; c += blockDim.x)
+            x[c] = zscore_one(x[c], q);
     }
 }
 
@@ -127,41 +267,56 @@ __global__ void k_transpose(const float *__restrict__ X, int rows_p, int cols_p,
         Y[(size_t)(bx + k) * rows_p + by + tx] = tile[tx][k];
 }
 
-// out[i] = sum_j X[i][j]^2 (+ diag[i]^2): one warp per row, FP64, fixed order.
+// x^2 into a compensated FP32 pair: x^2 = p + pe exactly, p through TwoSum
+__device__ __forceinline__ void sq_add(float x, float &acc, float &cmp)
+{
+    float p, pe;
+    two_prod(x, x, p, pe);
+    two_sum_add(acc, cmp, p);
+    cmp = __fadd_rn(cmp, pe);
+}
+
+// out[i] = sum_j X[i][j]^2 (+ diag[i]^2): one warp per row, lane l taking the
+// 4-wide column groups l, l + 32, ... (rows start 16-byte aligned), then the
+// ragged columns.  Compensated FP32 pairs folded into an FP64 total every 16
+// groups, FP64 across the warp: a fixed order.
 __global__ void k_row_norms(const float *__restrict__ X, int rows, int cols, int ld,
                             const double *diag, float *out)
 {
-    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (warp >= rows)
         return;
     const float *x = X + (size_t)warp * ld;
-    double acc = 0.0;
-    for (int c = lane; c < cols; c += 32) {
-        double v = (double)x[c];
-        acc += v * v;
+    const float4 *x4 = reinterpret_cast<const float4 *>(x);
+    const int c4n = cols >> 2;
+    double tot = 0.0;
+    for (int c0 = 0; c0 < c4n; c0 += 16 * 32) {
+        float acc = 0.0f, cmp = 0.0f;
+        const int ce = min(c4n, c0 + 16 * 32);
+#pragma unroll 4
+        for (int c = c0 + lane; c < ce; c += 32) {
+            const float4 v = x4[c];
+            sq_add(v.x, acc, cmp);
+            sq_add(v.y, acc, cmp);
+            sq_add(v.z, acc, cmp);
+            sq_add(v.w, acc, cmp);
+        }
+        tot += (double)acc + (double)cmp;
+    }
+    {
+        float acc = 0.0f, cmp = 0.0f;
+        for (int c = (c4n << 2) + lane; c < cols; c += 32)
+            sq_add(x[c], acc, cmp);
+        tot += (double)acc + (double)cmp;
     }
     for (int o = 16; o > 0; o >>= 1)
-        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        tot += __shfl_xor_sync(0xffffffffu, tot, o);
     if (lane == 0) {
         if (diag)
-            acc += diag[warp] * diag[warp];
-        out[warp] = (float)acc;
+            tot += diag[warp] * diag[warp];
+        out[warp] = (float)tot;
     }
-}
-
-// out[j] = sum_i X[i][j]^2: one thread per column, FP64, rows in order.
-__global__ void k_col_norms(const float *__restrict__ X, int rows, int cols, int ld, float *out)
-{
-    int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= cols)
-        return;
-    double acc = 0.0;
-    for (int i = 0; i < rows; ++i) {
-        double v = (double)X[(size_t)i * ld + j];
-        acc += v * v;
-    }
-    out[j] = (float)acc;
 }
 
 __global__ void k_scan_nonfinite(const float *__restrict__ X, long long n, int *flag)
@@ -274,24 +429,38 @@ cudaError_t launch_symmetrize(float *X, int n, int ld, cudaStream_t s)
     return cudaGetLastError();
 }
 
+// The element kernels read rows as float4: the row stride and base must
+// keep every row 16-byte aligned.
+static bool rows_aligned(const void *X, int ld) { return (ld & 3) == 0 && ((uintptr_t)X & 15) == 0; }
+
 cudaError_t launch_check_finite_sym(const float *X, int rows, int cols, int ld, bool sym,
                                     int *flags, cudaStream_t s)
 {
-    dim3 grid(ceil_div(cols, 256), rows < 65535 ? rows : 65535);
-    k_check_finite_sym<<<grid, 256, 0, s>>>(X, rows, cols, ld, sym ? 1 : 0, flags);
+    if (rows <= 0 || cols <= 0)
+        return cudaSuccess;
+    if (sym) {
+        if (rows != cols)
+            return cudaErrorInvalidValue;
+        const int nb = ceil_div(rows, 32);
+        const int npairs = (int)((long long)nb * (nb + 1) / 2);
+        k_check_finite_sym<<<npairs < 152 * 8 ? npairs : 152 * 8, 256, 0, s>>>(X, rows, ld, npairs, flags);
+    } else {
+        k_check_finite<<<rows < RED_BLOCKS ? rows : RED_BLOCKS, 256, 0, s>>>(X, rows, cols, ld, flags);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_zscore(float *X, int rows, int cols, int ld, double *stats, double *partials,
                           cudaStream_t s)
 {
+    if (!rows_aligned(X, ld) || ((uintptr_t)stats & 15))
+        return cudaErrorInvalidValue;
     double count = (double)rows * (double)cols;
-    k_stats_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(X, rows, cols, ld, 0, stats, partials);
+    k_stats_partial<0><<<RED_BLOCKS, RED_THREADS, 0, s>>>(X, rows, cols, ld, stats, partials);
     k_stats_final<<<1, RED_THREADS, 0, s>>>(partials, RED_BLOCKS, count, 0, stats);
-    k_stats_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(X, rows, cols, ld, 1, stats, partials);
+    k_stats_partial<1><<<RED_BLOCKS, RED_THREADS, 0, s>>>(X, rows, cols, ld, stats, partials);
     k_stats_final<<<1, RED_THREADS, 0, s>>>(partials, RED_BLOCKS, count, 1, stats);
-    dim3 grid(ceil_div(cols, 256), rows < 65535 ? rows : 65535);
-    k_apply_zscore<<<grid, 256, 0, s>>>(X, rows, cols, ld, stats);
+    k_apply_zscore<<<rows < 152 * 8 ? rows : 152 * 8, 256, 0, s>>>(X, rows, cols, ld, stats);
     return cudaGetLastError();
 }
 
@@ -317,13 +486,9 @@ cudaError_t launch_transpose(const float *X, int rows_p, int cols_p, float *Y, c
 cudaError_t launch_row_norms(const float *X, int rows, int cols, int ld, const double *diag,
                              float *out, cudaStream_t s)
 {
+    if (!rows_aligned(X, ld))
+        return cudaErrorInvalidValue;
     k_row_norms<<<ceil_div(rows * 32, 256), 256, 0, s>>>(X, rows, cols, ld, diag, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_col_norms(const float *X, int rows, int cols, int ld, float *out, cudaStream_t s)
-{
-    k_col_norms<<<ceil_div(cols, 256), 256, 0, s>>>(X, rows, cols, ld, out);
     return cudaGetLastError();
 }
 

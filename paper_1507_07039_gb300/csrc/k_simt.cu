@@ -221,15 +221,6 @@ __global__ void __launch_bounds__(NT, 2) k_phase1(Dev d, int cur)
 // on this GPU is far wider than the FP64 one.
 constexpr int RS_ROWS = 32, RS_GROUPS = 8;
 
-// s + x = s' + e exactly (round to nearest, no overflow): s' = fl(s + x)
-__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
-{
-    const float t = s + x;
-    const float z = t - s;
-    c += (s - (t - z)) + (x - z);
-    s = t;
-}
-
 template <int NV>
 __device__ __forceinline__ void slot_sums(const float *const (&src)[NV], int nslot, int ld, int x, bool ok,
                                           double (&out)[NV], double (*sh)[RS_GROUPS][RS_ROWS])

@@ -101,19 +101,6 @@ __device__ __forceinline__ float tanimoto_clamped(float num, float nx, float ny)
     return num * rsqrtf(fmaxf((nx + ny) - fabsf(num), 1e-30f));
 }
 
-// hi / lo of a whole array (padding stays zero because x is zero there); L may be NULL (hi only)
-__global__ void k_split(const float *__restrict__ X, size_t n, __nv_bfloat16 *__restrict__ H,
-                        __nv_bfloat16 *__restrict__ L)
-{
-    for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
-        __nv_bfloat16 hi, lo;
-        split_bf16(X[q], hi, lo);
-        H[q] = hi;
-        if (L)
-            L[q] = lo;
-    }
-}
-
 // hi / lo of two values at once, packed as BF16 pairs (first value in the low half)
 __device__ __forceinline__ void split_pair(float x0, float x1, uint32_t &hi, uint32_t &lo)
 {
@@ -130,16 +117,45 @@ __device__ __forceinline__ uint32_t e4m3x2(float x0, float x1, float s)
     return (uint32_t)__nv_cvt_float2_to_fp8x2(make_float2(x0 * s, x1 * s), __NV_SATFINITE, __NV_E4M3);
 }
 
-// E4M3 copy of a whole array, scaled by *scale (padding stays zero)
+// E4M3 copy of a whole array, scaled by *scale (padding stays zero): four
+// values per thread from one 16-byte load, one 4-byte store (all buffers are
+// whole allocations, so aligned; a misaligned one takes the scalar loop)
 __global__ void k_to_e4m3(const float *__restrict__ X, size_t n, uint8_t *__restrict__ Q, const float *scale)
 {
     const float s = scale ? *scale : 1.0f;
-    for (size_t q = 2 * ((size_t)blockIdx.x * blockDim.x + threadIdx.x); q < n;
-         q += 2 * (size_t)gridDim.x * blockDim.x) {
-        const uint32_t v = e4m3x2(X[q], q + 1 < n ? X[q + 1] : 0.0f, s);
-        Q[q] = (uint8_t)v;
-        if (q + 1 < n)
-            Q[q + 1] = (uint8_t)(v >> 8);
+    const size_t n4 = (((uintptr_t)X & 15) | ((uintptr_t)Q & 3)) ? 0 : n >> 2;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t q = t0; q < n4; q += stride) {
+        const float4 v = reinterpret_cast<const float4 *>(X)[q];
+        reinterpret_cast<uint32_t *>(Q)[q] = e4m3x2(v.x, v.y, s) | (e4m3x2(v.z, v.w, s) << 16);
+    }
+    for (size_t q = (n4 << 2) + t0; q < n; q += stride)
+        Q[q] = (uint8_t)e4m3x2(X[q], 0.0f, s);
+}
+
+// hi / lo of a whole array (padding stays zero because x is zero there); L may
+// be NULL (hi only).  Four values per thread from one 16-byte load, 8-byte
+// stores; a misaligned buffer takes the scalar loop.
+__global__ void k_split(const float *__restrict__ X, size_t n, __nv_bfloat16 *__restrict__ H,
+                        __nv_bfloat16 *__restrict__ L)
+{
+    const size_t n4 = (((uintptr_t)X & 15) | ((uintptr_t)H & 7) | ((uintptr_t)L & 7)) ? 0 : n >> 2;
+    const size_t t0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t q = t0; q < n4; q += stride) {
+        const float4 v = reinterpret_cast<const float4 *>(X)[q];
+        uint32_t h0, l0, h1, l1;
+        split_pair(v.x, v.y, h0, l0);
+        split_pair(v.z, v.w, h1, l1);
+        reinterpret_cast<uint2 *>(H)[q] = make_uint2(h0, h1);
+        if (L)
+            reinterpret_cast<uint2 *>(L)[q] = make_uint2(l0, l1);
+    }
+    for (size_t q = (n4 << 2) + t0; q < n; q += stride) {
+        __nv_bfloat16 hi, lo;
+        split_bf16(X[q], hi, lo);
+        H[q] = hi;
+        if (L)
+            L[q] = lo;
     }
 }
 

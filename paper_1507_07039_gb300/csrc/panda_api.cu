@@ -265,7 +265,7 @@ int derive_state(panda_ctx *c, bool split_diag)
     }
     CU(launch_transpose(d.W[c->cur], c->Tp, c->Gp, d.Wt[c->cur], c->stream));
     CU(launch_row_norms(d.W[c->cur], c->T, c->G, c->Gp, nullptr, d.rsqW, c->stream));
-    CU(launch_col_norms(d.W[c->cur], c->T, c->G, c->Gp, d.csqW, c->stream));
+    CU(launch_row_norms(d.Wt[c->cur], c->G, c->T, c->Tp, nullptr, d.csqW, c->stream));  // columns of W
     CU(launch_row_norms(d.Poff, c->T, c->T, c->Tp, d.pd, d.rsqP, c->stream));
     CU(launch_row_norms(d.Coff, c->G, c->G, c->Gp, d.cd, d.csqC, c->stream));
     if (tensor_prec(c->prec))

@@ -114,6 +114,37 @@ __device__ __forceinline__ float tanimoto_f(float num, float nx, float ny)
     return den > 0.0f ? num / den : 0.0f;
 }
 
+// ---- FP32 error-free transforms --------------------------------------------
+// This GPU's FP64 pipe issues about two operations per clock per SM, the FP32
+// pipe 128, so sums and products that want more than FP32 accuracy run as
+// FP32 pairs whose rounding errors are recovered exactly.
+
+// Knuth's TwoSum: s + x = s' + e exactly (round to nearest, no overflow),
+// s' = fl(s + x); the error e is added into the compensation c.
+__device__ __forceinline__ void two_sum_add(float &s, float &c, float x)
+{
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+}
+
+// a + b = s + e exactly
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float z = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, z)), __fsub_rn(b, z));
+}
+
+// a * b = p + e exactly (the product's rounding error from one FMA), barring
+// underflow of e
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
 // ---- launchers (k_setup.cu) ------------------------------------------------
 cudaError_t launch_check_finite_sym(const float *X, int rows, int cols, int ld, bool sym,
                                     int *flags, cudaStream_t s);
@@ -123,8 +154,6 @@ cudaError_t launch_split_diag(float *X, int n, int ld, double *d, float *df, cud
 cudaError_t launch_transpose(const float *X, int rows_p, int cols_p, float *Y, cudaStream_t s);
 cudaError_t launch_row_norms(const float *X, int rows, int cols, int ld, const double *diag,
                              float *out, cudaStream_t s);
-cudaError_t launch_col_norms(const float *X, int rows, int cols, int ld, float *out,
-                             cudaStream_t s);
 cudaError_t launch_diag_to_float(const double *d, float *df, int n, cudaStream_t s);
 cudaError_t launch_scan_nonfinite(const float *X, long long n, int *flag, cudaStream_t s);
 // X[r][c] = X[c][r] for r > c: the full matrix from its upper triangle

@@ -173,7 +173,7 @@ extern "C" int panda_step_static(int T, int G, float *dW, float *dP, float *dC, 
     SCU(launch_split_diag(d.Coff, G, d.Gp, d.cd, d.cdf, s));
     SCU(launch_transpose(d.W[0], d.Tp, d.Gp, d.Wt[0], s));
     SCU(launch_row_norms(d.W[0], T, G, d.Gp, nullptr, d.rsqW, s));
-    SCU(launch_col_norms(d.W[0], T, G, d.Gp, d.csqW, s));
+    SCU(launch_row_norms(d.Wt[0], G, T, d.Tp, nullptr, d.csqW, s));  // columns of W
     SCU(launch_row_norms(d.Poff, T, T, d.Tp, d.pd, d.rsqP, s));
     SCU(launch_row_norms(d.Coff, G, G, d.Gp, d.cd, d.csqC, s));
 

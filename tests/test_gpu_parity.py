@@ -92,6 +92,28 @@ def test_identity_priors(orc, prec, n):
     gh.assert_parity(g, o, prec, "identity priors")
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,offset", [("small64x256", 0.0), ("mid250x2100", 0.0), ("mid250x2100", 7.0)])
+def test_normalized_state_matches_oracle(orc, panda, name, offset, prec):
+    """The Z-scored networks a context starts from (Sec. II-A) against the
+    oracle's FP64 Z-score rounded to FP32.  The GPU sums in another order and
+    divides through FP32 pairs accurate to about 2^-44, so an entry may round
+    the other way when the exact quotient sits that close to a rounding
+    midpoint: at most one unit in the last place apart, and rarely (about
+    1e-6 of the entries expected).  An offset of 7 makes the mean large
+    against the spread of W0 and P0, the hardest case for the pair arithmetic."""
+    W0, P0, C0 = (x + np.float32(offset) for x in gh.inputs(name))
+    oW, oP, oC = orc.normalize(W0, P0, C0)
+    with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:
+        gW, gP, gC = ctx.get()
+    for label, g, o in (("W", gW, oW), ("P", gP, oP), ("C", gC, oC)):
+        o32 = o.astype(np.float32)
+        diff = np.abs(g.astype(np.float64) - o32.astype(np.float64))
+        ulp = np.spacing(np.maximum(np.abs(g), np.abs(o32))).astype(np.float64)
+        assert np.all(diff <= ulp), f"{label}: {np.max(diff / ulp):.1f} ulp"
+        assert np.count_nonzero(diff) <= 1e-4 * g.size + 2, f"{label}: {np.count_nonzero(diff)} of {g.size} differ"
+
+
 def test_alpha_zero_leaves_networks_unchanged(panda):
     W0, P0, C0 = gh.inputs("small64x256")
     with panda.PandaContext(W0, P0, C0) as ctx:
