@@ -221,9 +221,38 @@ __global__ void __launch_bounds__(NT, 2) k_phase1(Dev d, int cur)
 // on this GPU is far wider than the FP64 one.
 constexpr int RS_ROWS = 32, RS_GROUPS = 8;
 
+// This thread's slots g, g + 8, ... inside [lo, hi), in ascending order
 template <int NV>
-__device__ __forceinline__ void slot_sums(const float *const (&src)[NV], int nslot, int ld, int x, bool ok,
-                                          double (&out)[NV], double (*sh)[RS_GROUPS][RS_ROWS])
+__device__ __forceinline__ void slot_range(const float *const (&src)[NV], int lo, int hi, int ld, int x,
+                                           float (&s)[NV], float (&c)[NV])
+{
+    const int g = threadIdx.x / RS_ROWS;
+    int b = lo + (((g - lo) % RS_GROUPS) + RS_GROUPS) % RS_GROUPS;
+    // four slots' loads in flight at a time; the additions keep the order
+    for (; b + 3 * RS_GROUPS < hi; b += 4 * RS_GROUPS) {
+        float t[NV][4];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                t[v][u] = src[v][(size_t)(b + u * RS_GROUPS) * ld + x];
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                two_sum_add(s[v], c[v], t[v][u]);
+    }
+    for (; b < hi; b += RS_GROUPS)
+#pragma unroll
+        for (int v = 0; v < NV; ++v)
+            two_sum_add(s[v], c[v], src[v][(size_t)b * ld + x]);
+}
+
+// Sums over the slots in [lo0, hi0) and [lo1, hi1) (lo1 >= hi0): slots outside
+// them hold zeros, whose additions would change nothing.
+template <int NV>
+__device__ __forceinline__ void slot_sums(const float *const (&src)[NV], int lo0, int hi0, int lo1, int hi1, int ld,
+                                          int x, bool ok, double (&out)[NV], double (*sh)[RS_GROUPS][RS_ROWS])
 {
     const int lx = threadIdx.x & (RS_ROWS - 1), g = threadIdx.x / RS_ROWS;
     float s[NV], c[NV];
@@ -231,25 +260,8 @@ __device__ __forceinline__ void slot_sums(const float *const (&src)[NV], int nsl
     for (int v = 0; v < NV; ++v)
         s[v] = c[v] = 0.0f;
     if (ok) {
-        // four slots' loads in flight at a time; the additions keep the order b = g, g + 8, ...
-        int b = g;
-        for (; b + 3 * RS_GROUPS < nslot; b += 4 * RS_GROUPS) {
-            float t[NV][4];
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    t[v][u] = src[v][(size_t)(b + u * RS_GROUPS) * ld + x];
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    two_sum_add(s[v], c[v], t[v][u]);
-        }
-        for (; b < nslot; b += RS_GROUPS)
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-                two_sum_add(s[v], c[v], src[v][(size_t)b * ld + x]);
+        slot_range<NV>(src, lo0, hi0, ld, x, s, c);
+        slot_range<NV>(src, lo1, hi1, ld, x, s, c);
     }
 #pragma unroll
     for (int v = 0; v < NV; ++v)
@@ -291,7 +303,7 @@ __device__ __forceinline__ void reduce_wnorms_block(const Dev &d, int b)
     const bool ok = x < (rows ? d.T : d.G);
     const float *const src[1] = {rows ? d.wrow_part : d.wcol_part};
     double out[1];
-    slot_sums<1>(src, rows ? d.nbG : d.nbT, rows ? d.Tp : d.Gp, x, ok, out, sh);
+    slot_sums<1>(src, 0, rows ? d.nbG : d.nbT, 0, 0, rows ? d.Tp : d.Gp, x, ok, out, sh);
     if (threadIdx.x >= RS_ROWS)
         return;
     if (ok)
@@ -453,11 +465,18 @@ __device__ __forceinline__ void fin_block(const Dev &d, int b)
     const int i = ((isP ? b : b - bT) * RS_ROWS) + (threadIdx.x & (RS_ROWS - 1));
     const int n = isP ? d.T : d.G;       // network size
     const bool ok = i < n;
-    const int nb = isP ? (d.nsP ? d.nsP : d.nbT) : (d.nsC ? d.nsC : d.nbG);  // partial-sum slots
     const int ld = isP ? d.Tp : d.Gp;
     const float *const src[3] = {isP ? d.ps_sum : d.cs_sum, isP ? d.ps_sq : d.cs_sq, isP ? d.ps_vsq : d.cs_vsq};
     double sums[3];
-    slot_sums<3>(src, nb, ld, i, ok, sums, sh);
+    if (d.tri_slots) {
+        // a row of 256-block b has row-role partials in slots [b, nb) (tiles (b, bn >= b)) and
+        // column-role partials in [nb, nb + 2 b + 2) (tiles (bm <= b, b), one per CTA of the pair)
+        const int nb = ceil_div(ld, 256), b256 = ((isP ? b : b - bT) * RS_ROWS) >> 8;
+        slot_sums<3>(src, b256, nb, nb, nb + 2 * b256 + 2, ld, i, ok, sums, sh);
+    } else {
+        const int ns = isP ? (d.nsP ? d.nsP : d.nbT) : (d.nsC ? d.nsC : d.nbG);
+        slot_sums<3>(src, 0, ns, 0, 0, ld, i, ok, sums, sh);
+    }
     if (threadIdx.x >= RS_ROWS)
         return;
     float nrm = 0.0f;  // the row's new squared norm (0 past the network)

@@ -147,6 +147,7 @@ int plan_memory(panda_ctx *c)
     // for the column role (see k_tc.cu)
     d.nsP = tensor_prec(c->prec) ? 3 * ceil_div(c->Tp, 256) : c->nbT;
     d.nsC = tensor_prec(c->prec) ? 3 * ceil_div(c->Gp, 256) : c->nbG;
+    d.tri_slots = tensor_prec(c->prec) ? 1 : 0;
     DALLOC(d.ps_sum, (size_t)d.nsP * Tp);
     DALLOC(d.ps_sq, (size_t)d.nsP * Tp);
     DALLOC(d.ps_vsq, (size_t)d.nsP * Tp);

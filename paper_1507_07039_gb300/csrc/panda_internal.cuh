@@ -56,6 +56,9 @@ struct Dev {
     float *ps_sum, *ps_sq, *ps_vsq;  // nsP x Tp  row partials of P'
     float *cs_sum, *cs_sq, *cs_vsq;  // nsC x Gp  row partials of C'
     int nsP, nsC;                    // partial-sum slots per row (0: one per 128-row block)
+    int tri_slots;                   // 1: the tensor-core layout of those slots (row roles in
+                                     // [0, nb), column roles from nb, nb = 256-blocks); 0: one
+                                     // slot per 128-block, every slot written
     Ctl *ctl;
     double *hist;                // HIST_CAP
     double *e2tab;               // HIST_CAP + 1: e^{2 alpha t}, computed on the host
