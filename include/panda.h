@@ -88,7 +88,9 @@ void panda_default_opts(panda_opts *o);
  * copied and not retained.  P0 and C0 must be exactly symmetric (PANDA_EASYM)
  * and every entry finite (PANDA_ENONFINITE).  With opts->normalize each
  * network is Z-scored with one global mean and population standard deviation
- * computed in FP64 (PANDA_EDEGENERATE when that deviation is 0).  o may be
+ * accurate to FP64 (compensated sums; PANDA_EDEGENERATE when that deviation is
+ * 0); each Z-scored entry is within one FP32 ulp of the FP64 value rounded to
+ * FP32, and equal to it except near a rounding midpoint.  o may be
  * NULL for the defaults.  The library owns all device state; it runs on the
  * current CUDA device and on its own non-blocking stream.  On error *out is
  * set to NULL and nothing is leaked. */

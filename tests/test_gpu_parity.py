@@ -210,6 +210,43 @@ def test_error_codes(panda):
         assert not conv and n == 2
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("T,G", [(3, 31), (33, 97), (40, 300)])
+def test_validation_finds_every_position(panda, prec, T, G):
+    """The create-time checks read P and C as mirror pairs of 32 x 32 blocks:
+    one asymmetric entry or one non-finite entry is found wherever it sits
+    (first and last block, diagonal blocks, across a block edge, the ragged
+    last block), and exactly symmetric finite inputs pass."""
+    rng = np.random.default_rng(T * 1000 + G)
+    W0 = rng.standard_normal((T, G)).astype(np.float32)
+    P0 = gh.random_symmetric(rng, T)
+    C0 = gh.random_symmetric(rng, G)
+    with panda.PandaContext(W0, P0, C0, prec=prec, normalize=False) as ctx:
+        gW, gP, gC = ctx.get()
+    assert np.array_equal(gW, W0) and np.array_equal(gP, P0) and np.array_equal(gC, C0)
+
+    def expect(code, W=W0, P=P0, C=C0):
+        with pytest.raises(panda.PandaError) as e:
+            panda.PandaContext(W, P, C, prec=prec, normalize=False)
+        assert e.value.code == code
+
+    for X, n, which in ((C0, G, "C"), (P0, T, "P")):
+        pos = {(0, 1), (1, 0), (n - 1, n - 2), (n - 2, n - 1), (0, n - 1), (n - 1, 0)}
+        if n > 32:
+            pos |= {(31, 32), (32, 31), (n - 1, 32), (5, n - 1)}
+        for i, j in sorted(pos):
+            bad = X.copy()
+            bad[i, j] += 0.5
+            expect(-5, **{which: bad})
+        for i, j in sorted(pos | {(0, 0), (n - 1, n - 1)}):
+            bad = X.copy()
+            bad[i, j] = np.nan if (i + j) % 2 else np.inf
+            expect(-4, **{which: bad})
+    bad = W0.copy()
+    bad[T - 1, G - 1] = -np.inf
+    expect(-4, W=bad)
+
+
 def test_allocation_cap_gives_enomem(panda, monkeypatch):
     W0, P0, C0 = gh.inputs("small64x256")
     monkeypatch.setenv("PANDA_ALLOC_LIMIT_BYTES", "100000")
