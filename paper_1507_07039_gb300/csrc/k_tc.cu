@@ -1121,10 +1121,11 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 }
                 // column sums of s under D2 (from registers; v sums come from the staged block)
                 if (SIM_SIGMA) {
+                    float sq[16];  // old[] holds the new values, staged below; acc is consumed here
 #pragma unroll
                     for (int q = 0; q < 16; ++q)
-                        old[q] = acc[q] * acc[q];
-                    const float t1 = lane_transpose_sum16(old);
+                        sq[q] = acc[q] * acc[q];
+                    const float t1 = lane_transpose_sum16(sq);
                     const float t0 = lane_transpose_sum16(acc);
                     if (lane < 16) {
                         colred[(wq * NS + 1) * N2 + cc + lane] = t1;

@@ -24,7 +24,10 @@ Tolerances (FP32 epilogues; derivation in the design notes):
     iteration); over the parity cases the worst error is 4.2e-2 (W) and 4.0e-2
     (a diagonal).  Bound: 1e-1 for W, off-diagonal and diagonal, which any
     wrong scale (a factor of 2 at least) or a missing term exceeds.  Compared
-    at the oracle's iteration count.
+    at the oracle's iteration count.  Under diagonal rule D0 (Eq. 6 as printed,
+    no alpha on the diagonal increment) the diagonals grow undamped and the
+    off-diagonal C error of FP8MIX reaches 0.108 (40 x 150, 6 iterations):
+    bound 2e-1 for that rule in this mode (FP8MIX_D0).
 """
 from __future__ import annotations
 
@@ -38,6 +41,9 @@ TOL = {
     2: dict(W=3e-3, off=3e-3, diag=3e-3),  # PANDA_BF16X2
     3: dict(W=1e-1, off=1e-1, diag=1e-1),  # PANDA_FP8MIX
 }
+
+
+FP8MIX_D0 = dict(W=1e-1, off=2e-1, diag=1e-1)
 
 
 def f32_alpha(alpha: float) -> float:
@@ -79,8 +85,8 @@ def errors(g, o):
     return out
 
 
-def assert_parity(g, o, prec=0, what=""):
-    t = TOL[prec]
+def assert_parity(g, o, prec=0, what="", tol=None):
+    t = tol or TOL[prec]
     e = errors(g, o)
     assert e["W"] <= t["W"], f"{what} W err {e['W']:.3e} > {t['W']:.1e} ({e})"
     for k in ("Poff", "Coff"):

@@ -70,6 +70,26 @@ def test_batch_runs_in_pieces(prec):
     assert epi == weights[int(np.argmin(trial_ms))]
 
 
+@pytest.mark.parametrize("prec", [1, 3])
+def test_batch_diagonal_rule_d2(prec):
+    """The set engine under rule D2 (its phase 2 also sums the new
+    similarities per row): every network as in its single run, bit for bit,
+    and close to the oracle."""
+    from paper_1507_07039_gb300 import panda
+    nets = uneven_set(4, seed=55)
+    with panda.PandaBatch(nets, prec=prec, diag=2) as b:
+        conv, iters, hl = b.run(0.1, 0.0, 5)
+        got = [b.get(k) for k in range(len(b))]
+    orc = Oracle()
+    orc.set_threads(os.cpu_count() or 1)
+    for k, (W0, P0, C0) in enumerate(nets):
+        single = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 5, diag=2)
+        for a, g in zip((single["W"], single["P"], single["C"]), got[k]):
+            assert np.array_equal(a, g), f"network {k} differs from its single run"
+        o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 5, diag=2)
+        gh.assert_parity({"W": got[k][0], "P": got[k][1], "C": got[k][2]}, o, prec, f"network {k}")
+
+
 def test_batch_errors_name_the_network():
     from paper_1507_07039_gb300 import panda
     nets = uneven_set(3)
