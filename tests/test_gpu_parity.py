@@ -59,7 +59,8 @@ def test_mid_network_fixed_iterations(orc, prec):
     gh.assert_parity(g, o, prec, "mid")
 
 
-EDGE_SHAPES = [(1, 1), (1, 5), (3, 1), (2, 3), (5, 130), (130, 7), (129, 257), (128, 128), (200, 385)]
+EDGE_SHAPES = [(1, 1), (1, 5), (3, 1), (2, 3), (5, 130), (130, 7), (129, 257), (128, 128), (200, 385), (256, 512),
+               (257, 256)]
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -178,19 +179,39 @@ def test_set_state_continues_close(panda, prec):
     assert np.max(np.abs(ref[0] - got[0])) < (1e-5 if prec == 0 else 1e-4)
 
 
-def test_device_pointer_create_matches_host(panda):
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_device_pointer_create_matches_host(panda, prec):
+    """panda_create_device on torch-owned buffers and panda_get_device into
+    them give the host path's results bit for bit (W, P and C)."""
     import torch
     W0, P0, C0 = gh.inputs("small64x256")
     dW, dP, dC = (torch.from_numpy(x).cuda() for x in (W0, P0, C0))
     stream = torch.cuda.current_stream().cuda_stream
     torch.cuda.synchronize()
-    with panda.PandaContext(dW, dP, dC, device=True, stream=stream) as a:
+    with panda.PandaContext(dW, dP, dC, prec=prec, device=True, stream=stream) as a:
         a.run(0.1, 0.0, 4)
-        oW = torch.empty_like(dW)
-        panda.panda_get_device(a.h, oW, None, None)
-        got = oW.cpu().numpy()
-    ref = gh.gpu_run(W0, P0, C0, 0, 0.1, 0.0, 4)["W"]
-    assert np.array_equal(got, ref)
+        outs = [torch.empty_like(x) for x in (dW, dP, dC)]
+        panda.panda_get_device(a.h, *outs)
+        torch.cuda.synchronize()
+        got = [x.cpu().numpy() for x in outs]
+    ref = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 4)
+    for g, k in zip(got, ("W", "P", "C")):
+        assert np.array_equal(g, ref[k]), k
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_start_index_t0(orc, panda, prec):
+    """opts.t0 = 7: the first iteration uses t = 8 in the e^{2 alpha t} factor
+    of the diagonals (Eq. 6), against the oracle started at the same t."""
+    W0, P0, C0 = gh.inputs("small64x256")
+    W, P, C = orc.normalize(W0, P0, C0)
+    oW, oP, oC, n, hist, _ = orc.run(W, P, C, gh.f32_alpha(0.1), 0.0, 4, 7)
+    with panda.PandaContext(W0, P0, C0, prec=prec, t0=7) as ctx:
+        conv, k, h = ctx.run(0.1, 0.0, 4)
+        gW, gP, gC = ctx.get()
+        t = ctx.info()[3]
+    assert k == 4 and t == 11
+    gh.assert_parity({"W": gW, "P": gP, "C": gC}, {"W": oW, "P": oP, "C": oC}, prec, "t0 = 7")
 
 
 def test_error_codes(panda):
