@@ -37,6 +37,9 @@ MUTANTS = {
     "diag_sample_std": ("return sqrt(ss / (double)(n - 1));", "return sqrt(ss / (double)(n > 2 ? n - 2 : 1));"),
     "diag_includes_diagonal": ("    double mean = s / (double)(n - 1);",
                                "    s += X[(long)i * n + i];\n    double mean = s / (double)(n - 1);"),
+    "diag_d2_sigma_of_entries": ("const double *src = (rule == ORACLE_DIAG_D2) ? sim : Xn;",
+                                 "const double *src = Xn;"),
+    "diag_d0_damped_like_d1": ("double gain = (rule == ORACLE_DIAG_D0) ? 1.0 : alpha;", "double gain = alpha;"),
     "h_not_mean": ("*h = s / ((double)T * (double)G);", "*h = s / ((double)T);"),
     "zscore_sample_std": ("double sd = sqrt(ss / (double)n);", "double sd = sqrt(ss / (double)(n - 1));"),
     "stop_not_strict": ("if (h < tol) {", "if (h <= tol) {"),

@@ -16,14 +16,16 @@ from paper_1507_07039_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-def test_static_step_matches_context_step():
+@pytest.mark.parametrize("diag", [0, 1, 2])
+def test_static_step_matches_context_step(diag):
+    """Every diagonal rule (D1, D0, D2)."""
     import torch
     from paper_1507_07039_gb300 import panda
     T, G = 100, 300
     W0, P0, C0 = synth.make_inputs(synth.custom(T, G, 4242, n_samples=30, n_factors=3))
 
     # the allocating path: a context (no normalisation, so both see the same networks)
-    with panda.PandaContext(W0, P0, C0, normalize=False) as ctx:
+    with panda.PandaContext(W0, P0, C0, normalize=False, diag=diag) as ctx:
         ref_h = [ctx.step(0.1), ctx.step(0.1)]
         rW, rP, rC = ctx.get()
 
@@ -31,7 +33,7 @@ def test_static_step_matches_context_step():
     dW, dP, dC = (torch.from_numpy(x).cuda() for x in (W0, P0, C0))
     stream = torch.cuda.current_stream().cuda_stream
     torch.cuda.synchronize()
-    h = [panda.panda_step_static(T, G, dW, dP, dC, 0.1, t, stream=stream) for t in (1, 2)]
+    h = [panda.panda_step_static(T, G, dW, dP, dC, 0.1, t, diag=diag, stream=stream) for t in (1, 2)]
     sW, sP, sC = (x.cpu().numpy() for x in (dW, dP, dC))
 
     tol = gh.TOL[0]
