@@ -278,6 +278,32 @@ def test_validation_finds_every_position(panda, prec, T, G):
     expect(-4, W=bad)
 
 
+def test_device_bytes_follow_the_memory_plan(panda, monkeypatch):
+    """panda_device_bytes counts what a context holds: at least the padded
+    FP32 state (W and W^T twice, P, C), plus C's BF16 split in the tensor-core
+    modes (two copies under BF16X3, one under BF16X2); and a create capped at
+    that count succeeds while one byte less fails."""
+    W0, P0, C0 = gh.inputs("mid250x2100")
+    T, G = W0.shape
+    got = {}
+    for prec in (0, 1, 2):
+        with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:
+            got[prec] = ctx.device_bytes
+    Tp, Gp = -(-T // 128) * 128, -(-G // 128) * 128
+    assert got[0] >= 4 * (4 * Tp * Gp + Tp * Tp + Gp * Gp)
+    Tp, Gp = -(-T // 256) * 256, -(-G // 256) * 256
+    assert got[1] >= 4 * (4 * Tp * Gp + Tp * Tp + Gp * Gp) + 2 * 2 * Gp * Gp
+    assert got[2] >= 4 * (4 * Tp * Gp + Tp * Tp + Gp * Gp) + 2 * Gp * Gp
+    assert got[1] > got[2] > got[0]
+    monkeypatch.setenv("PANDA_ALLOC_LIMIT_BYTES", str(got[1]))
+    with panda.PandaContext(W0, P0, C0, prec=1) as ctx:
+        assert ctx.device_bytes == got[1]
+    monkeypatch.setenv("PANDA_ALLOC_LIMIT_BYTES", str(got[1] - 1))
+    with pytest.raises(panda.PandaError) as e:
+        panda.PandaContext(W0, P0, C0, prec=1)
+    assert e.value.code == -2
+
+
 def test_allocation_cap_gives_enomem(panda, monkeypatch):
     W0, P0, C0 = gh.inputs("small64x256")
     monkeypatch.setenv("PANDA_ALLOC_LIMIT_BYTES", "100000")
