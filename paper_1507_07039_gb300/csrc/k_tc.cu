@@ -972,9 +972,12 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                         const uint64_t al = sdesc_k_sw128(base + A_BYTES + off);
                         const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
                         const uint64_t bl = sdesc_k_sw128(base + 3 * A_BYTES + off);
-                        mma_bf16_pair(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
-                        if (d.split_b)
-                            mma_bf16_pair(dacc, ah, bl, idesc, 1u);
+                        if (d.split_b) {  // hi(A) once from shared memory for hi.hi and hi.lo
+                            mma_bf16_pair_fill_a(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                            mma_bf16_pair_lastuse_a(dacc, ah, bl, idesc, 1u);
+                        } else {
+                            mma_bf16_pair(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                        }
                         mma_bf16_pair(dacc, al, bh, idesc, 1u);
                     }
                     mma_commit_pair(&sy.empty[st]);
