@@ -90,6 +90,34 @@ def test_batch_diagonal_rule_d2(prec):
         gh.assert_parity({"W": got[k][0], "P": got[k][1], "C": got[k][2]}, o, prec, f"network {k}")
 
 
+@pytest.mark.parametrize("prec", [0, 1, 3])
+def test_batch_of_degenerate_shapes(prec):
+    """Single nodes, a single TF, single genes and ragged tiles in one set
+    (without normalisation: a 1 x 1 network has no spread to Z-score), each
+    network as in its single run, bit for bit, and close to the oracle."""
+    from paper_1507_07039_gb300 import panda
+    rng = np.random.default_rng(9)
+    nets = []
+    for T, G in ((1, 1), (1, 5), (3, 1), (2, 3), (129, 257), (300, 40)):
+        W0 = rng.standard_normal((T, G)).astype(np.float32)
+        nets.append((W0, gh.random_symmetric(rng, T), gh.random_symmetric(rng, G)))
+    with panda.PandaBatch(nets, prec=prec, normalize=False) as b:
+        conv, iters, hl = b.run(0.2, 0.0, 3)
+        got = [b.get(k) for k in range(len(b))]
+    assert list(iters) == [3] * len(nets)
+    orc = Oracle()
+    orc.set_threads(os.cpu_count() or 1)
+    for k, (W0, P0, C0) in enumerate(nets):
+        single = gh.gpu_run(W0, P0, C0, prec, 0.2, 0.0, 3, normalize=False)
+        for a, g in zip((single["W"], single["P"], single["C"]), got[k]):
+            assert np.array_equal(a, g), f"network {k} differs from its single run"
+        o = gh.oracle_run(orc, W0, P0, C0, 0.2, 0.0, 3, normalize=False)
+        gh.assert_parity({"W": got[k][0], "P": got[k][1], "C": got[k][2]}, o, prec, f"network {k}")
+    with pytest.raises(panda.PandaError) as e:
+        panda.PandaBatch([], prec=prec)
+    assert e.value.code == -1
+
+
 def test_batch_errors_name_the_network():
     from paper_1507_07039_gb300 import panda
     nets = uneven_set(3)
