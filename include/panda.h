@@ -188,7 +188,9 @@ int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, do
  * lo*hi, terms = 1 uses hi*hi only; terms + 10 runs the same product on CTA
  * pairs (cta_group::2 MMAs over 256 x 256 tiles); terms + 20 does so with B
  * held transposed on the device ([K][N]) and fed to the MMAs MN-major, the
- * form the availability product reads the lower triangle of C in; terms = 8
+ * form the availability product reads the lower triangle of C in; terms + 40
+ * holds both A ([K][M]) and B transposed and feeds both MN-major, terms + 50
+ * A only; terms = 8
  * rounds A and B to E4M3 (nearest even, saturating) and sums their products
  * on CTA pairs with kind::f8f6f4 MMAs (FP32 accumulation).  PANDA_EINVAL on
  * other terms or non-positive sizes; PANDA_EUNSUPPORTED off sm_103. */

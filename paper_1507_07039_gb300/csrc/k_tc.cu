@@ -333,8 +333,9 @@ struct SyncPair {
 };
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
-    k_tc_gemm_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl, int bmn, int fp8)
+    k_tc_gemm_pair(const __grid_constant__ GemmMaps maps, int Kp, int Np, float *D, Ctl *ctl, int mn, int fp8)
 {
+    // mn bit 0: B stored [K][N] and fed MN-major; bit 1: A stored [K][M] and fed MN-major
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
     SyncPair &sy = *reinterpret_cast<SyncPair *>(stages + PAIR_ST * PAIR_STAGE);
@@ -375,9 +376,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     tma_load_2d_pair(st + A_BYTES, &maps.Bh, fb, kb * 2 * BK, n0 + 128 * rank);
                     continue;
                 }
-                tma_load_2d_pair(st, &maps.Ah, fb, kb * BK, m0 + 128 * rank);
-                tma_load_2d_pair(st + A_BYTES, &maps.Al, fb, kb * BK, m0 + 128 * rank);
-                if (bmn) {  // B^T stored [K][N]: two 64 x 64 boxes per CTA half, N contiguous
+                if (mn & 2) {  // A^T stored [K][M]: two 64 x 64 boxes per CTA half, M contiguous
+                    for (int h = 0; h < 2; ++h) {
+                        tma_load_2d_pair(st + h * (A_BYTES / 2), &maps.Ah, fb, m0 + 128 * rank + 64 * h, kb * BK);
+                        tma_load_2d_pair(st + A_BYTES + h * (A_BYTES / 2), &maps.Al, fb, m0 + 128 * rank + 64 * h,
+                                         kb * BK);
+                    }
+                } else {
+                    tma_load_2d_pair(st, &maps.Ah, fb, kb * BK, m0 + 128 * rank);
+                    tma_load_2d_pair(st + A_BYTES, &maps.Al, fb, kb * BK, m0 + 128 * rank);
+                }
+                if (mn & 1) {  // B^T stored [K][N]: two 64 x 64 boxes per CTA half, N contiguous
                     for (int h = 0; h < 2; ++h) {
                         tma_load_2d_pair(st + 2 * A_BYTES + h * (A_BYTES / 2), &maps.Bh, fb,
                                          n0 + 128 * rank + 64 * h, kb * BK);
@@ -393,7 +402,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
         }
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {  // the even CTA issues the pair's MMAs
-            const uint32_t idesc = idesc_bf16_f32(256, PAIR_N) | (bmn ? IDESC_B_MN : 0u);
+            const uint32_t idesc =
+                idesc_bf16_f32(256, PAIR_N) | ((mn & 1) ? IDESC_B_MN : 0u) | ((mn & 2) ? IDESC_A_MN : 0u);
             int kb = 0;
             for (; kb < nk; ++kb) {
                 const int s = kb % PAIR_ST;
@@ -413,11 +423,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
                     const uint32_t off = kk * 32;
-                    const uint64_t ah = sdesc_k_sw128(base + off), al = sdesc_k_sw128(base + A_BYTES + off);
-                    const uint64_t bh = bmn ? sdesc_mn_sw128(base + 2 * A_BYTES + kk * 2048, A_BYTES / 2)
-                                            : sdesc_k_sw128(base + 2 * A_BYTES + off);
-                    const uint64_t bl = bmn ? sdesc_mn_sw128(base + 3 * A_BYTES + kk * 2048, A_BYTES / 2)
-                                            : sdesc_k_sw128(base + 3 * A_BYTES + off);
+                    const uint64_t ah = (mn & 2) ? sdesc_mn_sw128(base + kk * 2048, A_BYTES / 2)
+                                                 : sdesc_k_sw128(base + off);
+                    const uint64_t al = (mn & 2) ? sdesc_mn_sw128(base + A_BYTES + kk * 2048, A_BYTES / 2)
+                                                 : sdesc_k_sw128(base + A_BYTES + off);
+                    const uint64_t bh = (mn & 1) ? sdesc_mn_sw128(base + 2 * A_BYTES + kk * 2048, A_BYTES / 2)
+                                                 : sdesc_k_sw128(base + 2 * A_BYTES + off);
+                    const uint64_t bl = (mn & 1) ? sdesc_mn_sw128(base + 3 * A_BYTES + kk * 2048, A_BYTES / 2)
+                                                 : sdesc_k_sw128(base + 3 * A_BYTES + off);
                     mma_bf16_pair(sy.tmem, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
                     mma_bf16_pair(sy.tmem, ah, bl, idesc, 1u);
                     mma_bf16_pair(sy.tmem, al, bh, idesc, 1u);
@@ -1762,8 +1775,18 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     TRY(cudaMemset(ctl, 0, sizeof(Ctl)));
     TRY(cudaMemset(dA, 0, (size_t)Mp * Kp * 4));
     TRY(cudaMemset(dB, 0, (size_t)Np * Kp * 4));
-    TRY(cudaMemcpy2D(dA, (size_t)Kp * 4, A, (size_t)K * 4, (size_t)K * 4, M, cudaMemcpyHostToDevice));
-    if (pair == 2) {  // B^T, [Kp][Np], for the MN-major B loads
+    // pair 2: B held transposed and fed MN-major; 4: A and B; 5: A only
+    const int mn = pair == 2 ? 1 : pair == 4 ? 3 : pair == 5 ? 2 : 0;
+    if (mn & 2) {  // A^T, [Kp][Mp], for the MN-major A loads
+        std::vector<float> at((size_t)K * M);
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < K; ++k)
+                at[(size_t)k * M + m] = A[(size_t)m * K + k];
+        TRY(cudaMemcpy2D(dA, (size_t)Mp * 4, at.data(), (size_t)M * 4, (size_t)M * 4, K, cudaMemcpyHostToDevice));
+    } else {
+        TRY(cudaMemcpy2D(dA, (size_t)Kp * 4, A, (size_t)K * 4, (size_t)K * 4, M, cudaMemcpyHostToDevice));
+    }
+    if (mn & 1) {  // B^T, [Kp][Np], for the MN-major B loads
         std::vector<float> bt((size_t)K * N);
         for (int n = 0; n < N; ++n)
             for (int k = 0; k < K; ++k)
@@ -1795,9 +1818,14 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
         TRY(cudaMemset(Al, 0, (size_t)Mp * Kp * 2));
         TRY(cudaMemset(Bl, 0, (size_t)Np * Kp * 2));
     }
-    TRY(make_map(&maps.Ah, Ah, Mp, Kp, 128));
-    TRY(make_map(&maps.Al, Al, Mp, Kp, 128));
-    if (pair == 2) {
+    if (mn & 2) {
+        TRY(make_map(&maps.Ah, Ah, Kp, Mp, 64));
+        TRY(make_map(&maps.Al, Al, Kp, Mp, 64));
+    } else {
+        TRY(make_map(&maps.Ah, Ah, Mp, Kp, 128));
+        TRY(make_map(&maps.Al, Al, Mp, Kp, 128));
+    }
+    if (mn & 1) {
         TRY(make_map(&maps.Bh, Bh, Kp, Np, 64));
         TRY(make_map(&maps.Bl, Bl, Kp, Np, 64));
     } else {
@@ -1806,8 +1834,7 @@ cudaError_t tc_selftest_gemm(int M, int N, int K, const float *A, const float *B
     }
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
     if (pair)
-        k_tc_gemm_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl,
-                                                                                    pair == 2, 0);
+        k_tc_gemm_pair<<<dim3(Mp / 128, Np / PAIR_N), THREADS, pair_smem()>>>(maps, Kp, Np, dD, ctl, mn, 0);
     else
         k_tc_selftest<<<dim3(Mp / 128, Np / 128), THREADS, st_smem>>>(maps, Kp, Np, dD, ctl, stall_kb);
     TRY(cudaGetLastError());

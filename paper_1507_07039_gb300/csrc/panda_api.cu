@@ -961,15 +961,16 @@ int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, 
 {
     // terms + 10: the same product on CTA pairs (cta_group::2, 256 x 256 tiles);
     // terms + 20: on CTA pairs with B stored transposed and loaded MN-major;
+    // terms + 40: A and B both so; terms + 50: A only;
     // terms = 8: E4M3 operands, one term, on CTA pairs
     int pair = terms / 10;
     terms %= 10;
     if (terms == 8 && pair == 0) {
         pair = 3;
         terms = 1;
-    }
-    if (pair > 3)
+    } else if (pair == 3 || pair > 5) {
         return set_err(nullptr, PANDA_EINVAL, "panda_selftest_tc_gemm: bad argument");
+    }
     if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !D || (terms != 1 && terms != 3))
         return set_err(nullptr, PANDA_EINVAL, "panda_selftest_tc_gemm: bad argument");
     if (!tc_supported())

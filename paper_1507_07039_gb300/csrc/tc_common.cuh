@@ -149,6 +149,8 @@ __device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t mn_a
 
 // Instruction-descriptor bit that marks the B operand MN-major ("transpose B").
 constexpr uint32_t IDESC_B_MN = 1u << 16;
+// instruction-descriptor bit for an A operand read MN-major from shared memory
+constexpr uint32_t IDESC_A_MN = 1u << 15;
 
 // Instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator,
 // both operands K-major: D format (bits 4-5) = F32, A format (7-9) = BF16,

@@ -89,6 +89,28 @@ def test_cta_pair_product_mn_major_b(M, N, K):
     assert np.max(np.abs(D3 - panda.panda_selftest_tc_gemm(A, B, terms=13))) / scale < 1e-5
 
 
+@pytest.mark.parametrize("mode", [40, 50])
+@pytest.mark.parametrize("M,N,K", [(256, 256, 64), (300, 600, 1000), (512, 256, 130)])
+def test_cta_pair_product_mn_major_a(mode, M, N, K):
+    """CTA pairs with A held transposed ([K][M], M contiguous) and fed to the
+    MMAs MN-major, with B so too (mode 40) or K-major (mode 50): the same
+    products as the K-major form."""
+    from paper_1507_07039_gb300 import panda
+    rng = np.random.default_rng(7 * M + N + K + mode)
+    A = rng.standard_normal((M, K)).astype(np.float32)
+    B = rng.standard_normal((N, K)).astype(np.float32)
+    Ah, Al = bf16_split(A)
+    Bh, Bl = bf16_split(B)
+    D1 = panda.panda_selftest_tc_gemm(A, B, terms=mode + 1)
+    ref1 = Ah @ Bh.T
+    scale = max(1.0, np.max(np.abs(ref1)))
+    assert np.max(np.abs(D1 - ref1)) / scale < 2e-6
+    D3 = panda.panda_selftest_tc_gemm(A, B, terms=mode + 3)
+    ref3 = Ah @ Bh.T + Ah @ Bl.T + Al @ Bh.T
+    assert np.max(np.abs(D3 - ref3)) / scale < 1e-5
+    assert np.max(np.abs(D3 - panda.panda_selftest_tc_gemm(A, B, terms=13))) / scale < 1e-5
+
+
 def e4m3(x: np.ndarray) -> np.ndarray:
     """x rounded to E4M3 (nearest even), as float64 (|x| stays below 448 here)."""
     import torch
