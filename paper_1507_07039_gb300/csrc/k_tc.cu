@@ -50,7 +50,7 @@ using namespace tc;
 struct TcMaps {  // split copies, K-major, boxes of 64 x 128 (one CTA's half of a 256-row tile)
     CUtensorMap Ph, Pl;              // P_off split   [Tp][Tp]
     CUtensorMap Wh[2], Wl[2];        // W split       [Tp][Gp]
-    CUtensorMap Wth[2], Wtl[2];      // W^T split     [Gp][Tp]
+    CUtensorMap Whm[2], Wlm[2];      // the same arrays in boxes of 64 x 64: W^T operands, MN-major
     CUtensorMap Ch, Cl;              // C_off split   [Gp][Gp]
     CUtensorMap Chm, Clm;            // the same arrays in boxes of 64 x 64, for MN-major loads
     CUtensorMap W8[2], Wt8[2], C8;   // FP8MIX: E4M3 copies, boxes of 128 B x 128 rows
@@ -552,13 +552,16 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                 if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half, 2 of E4M3
                     mbar_arrive_expect_tx(&sy.full[st], (kb >= nR && d.fp8 ? 4 : (d.split_b ? 8 : 6)) * A_BYTES);
                 uint8_t *b = stages + (size_t)st * STAGE1;
-                if (kb < nR) {  // responsibility: P_off rows x W^T rows, K over TFs
+                if (kb < nR) {  // responsibility: P_off rows x W columns, K over TFs
                     const int k = kb * BK;
                     tma_load_2d_pair(b, &maps.Ph, fb, k, m0);
                     tma_load_2d_pair(b + A_BYTES, &maps.Pl, fb, k, m0);
-                    tma_load_2d_pair(b + 2 * A_BYTES, &maps.Wth[cur], fb, k, nb0);
-                    if (d.split_b)
-                        tma_load_2d_pair(b + 3 * A_BYTES, &maps.Wtl[cur], fb, k, nb0);
+                    for (int h = 0; h < 2; ++h) {  // W rows k.. k + 63, this CTA's 128 genes: MN-major
+                        tma_load_2d_pair(b + 2 * A_BYTES + h * (A_BYTES / 2), &maps.Whm[cur], fb, nb0 + 64 * h, k);
+                        if (d.split_b)
+                            tma_load_2d_pair(b + 3 * A_BYTES + h * (A_BYTES / 2), &maps.Wlm[cur], fb, nb0 + 64 * h,
+                                             k);
+                    }
                 } else if (d.fp8) {  // availability on E4M3 copies (C8 holds both triangles)
                     const int k = (kb - nR) * 2 * BK;
                     tma_load_2d_pair(b, &maps.W8[cur], fb, k, m0);
@@ -603,7 +606,7 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                     mma_commit_pair(&sy.empty[st]);
                     continue;
                 }
-                const bool bmn = kb >= nR && (kb - nR) * BK < n0;  // B block loaded MN-major
+                const bool bmn = kb < nR || (kb - nR) * BK < n0;  // B block loaded MN-major
                 const uint32_t id = bmn ? (idesc | IDESC_B_MN) : idesc;
 #pragma unroll
                 for (int kk = 0; kk < BK / 16; ++kk) {
@@ -632,7 +635,7 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
         const int nx = cur ^ 1;
         const float *W = d.W[cur];
         float *Wn = d.W[nx];
-        __nv_bfloat16 *Wh = d.Wh[nx], *Wl = d.Wl[nx], *Wth = d.Wth[nx], *Wtl = d.Wtl[nx];
+        __nv_bfloat16 *Wh = d.Wh[nx], *Wl = d.Wl[nx];
         // FP8MIX: the A-num accumulator holds the scaled E4M3 products; W' gets E4M3 copies too
         const bool q8 = d.fp8 != 0;
         const float ainv = q8 ? 1.0f / (d.f8[cur] * d.f8[2]) : 1.0f, s8 = q8 ? d.f8[3] : 1.0f;
@@ -701,8 +704,8 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                 if (q8)
                     *reinterpret_cast<uint32_t *>(d.W8[nx] + ro) = e4m3x2(f[0], f[1], s8) | e4m3x2(f[2], f[3], s8) << 16;
             }
-            // (b) the transposed split copies: lane l takes column (l & 15), rows 16 (l >> 4) + 0..15,
-            //     and the column sums of W'^2 over the warp's 32 rows
+            // (b) the column sums of W'^2 over the warp's 32 rows (lane l: column (l & 15), rows
+            //     16 (l >> 4) + 0..15) and, under FP8MIX, the transposed E4M3 copy
             {
                 const int col = lane & 15, h16 = 16 * (lane >> 4);
                 float g[16];
@@ -716,14 +719,8 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                 c2 += __shfl_xor_sync(0xffffffffu, c2, 16);
                 if (lane < 16)
                     colred[wq * 256 + cc + lane] = c2;
-                uint32_t hv[8], lv[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    split_pair(g[2 * q], g[2 * q + 1], hv[q], lv[q]);
-                const size_t to = (size_t)(j0 + col) * d.Tp + k0 + h16;
-                st16_packed(Wth + to, hv, 0xffffu);
-                st16_packed(Wtl + to, lv, 0xffffu);
                 if (q8) {
+                    const size_t to = (size_t)(j0 + col) * d.Tp + k0 + h16;
                     uint32_t p8[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
@@ -916,8 +913,10 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 const int m0 = ((tile >> 16) & 0x7fff) * N2 + 128 * rank, n0 = (tile & 0xffff) * N2 + 128 * rank;
                 const bool q8 = d.fp8 && !isP;  // FP8MIX: C tiles from the E4M3 copy of W'^T, one term
                 const int nk = isP ? d.Gp / BK : d.Tp / (q8 ? 2 * BK : BK);
-                const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Wth[cur];
-                const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wtl[cur];
+                // P tiles: rows of W' (K over genes, K-major); C tiles: columns of W' (K over TFs),
+                // read from the same arrays MN-major
+                const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Whm[cur];
+                const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wlm[cur];
                 for (int kb = 0; kb < nk; ++kb, ++g) {
                     const int st = g % ST2;
                     if (!wait_bounded(&sy.empty[st], ((uint32_t)(g / ST2) & 1u) ^ 1u, &sy.abort, d.ctl)) {
@@ -933,11 +932,22 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                         tma_load_2d_pair(b + A_BYTES, &maps.Wt8[cur], fb, kb * 2 * BK, n0);
                         continue;
                     }
-                    tma_load_2d_pair(b, mh, fb, kb * BK, m0);
-                    tma_load_2d_pair(b + A_BYTES, ml, fb, kb * BK, m0);
-                    tma_load_2d_pair(b + 2 * A_BYTES, mh, fb, kb * BK, n0);
-                    if (d.split_b)
-                        tma_load_2d_pair(b + 3 * A_BYTES, ml, fb, kb * BK, n0);
+                    if (isP) {
+                        tma_load_2d_pair(b, mh, fb, kb * BK, m0);
+                        tma_load_2d_pair(b + A_BYTES, ml, fb, kb * BK, m0);
+                        tma_load_2d_pair(b + 2 * A_BYTES, mh, fb, kb * BK, n0);
+                        if (d.split_b)
+                            tma_load_2d_pair(b + 3 * A_BYTES, ml, fb, kb * BK, n0);
+                        continue;
+                    }
+                    for (int h = 0; h < 2; ++h) {  // two 64 x 64 boxes per 128 genes
+                        const uint32_t o = h * (A_BYTES / 2);
+                        tma_load_2d_pair(b + o, mh, fb, m0 + 64 * h, kb * BK);
+                        tma_load_2d_pair(b + A_BYTES + o, ml, fb, m0 + 64 * h, kb * BK);
+                        tma_load_2d_pair(b + 2 * A_BYTES + o, mh, fb, n0 + 64 * h, kb * BK);
+                        if (d.split_b)
+                            tma_load_2d_pair(b + 3 * A_BYTES + o, ml, fb, n0 + 64 * h, kb * BK);
+                    }
                 }
             }
             sy.issued = g;
@@ -978,20 +988,25 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                         mma_commit_pair(&sy.empty[st]);
                         continue;
                     }
+                    const bool mn = tile >= 0;  // C tiles: both operands MN-major
+                    const uint32_t id = mn ? (idesc | IDESC_A_MN | IDESC_B_MN) : idesc;
 #pragma unroll
                     for (int kk = 0; kk < BK / 16; ++kk) {
-                        const uint32_t off = kk * 32;
-                        const uint64_t ah = sdesc_k_sw128(base + off);
-                        const uint64_t al = sdesc_k_sw128(base + A_BYTES + off);
-                        const uint64_t bh = sdesc_k_sw128(base + 2 * A_BYTES + off);
-                        const uint64_t bl = sdesc_k_sw128(base + 3 * A_BYTES + off);
+                        const uint32_t off = kk * 32, moff = kk * 2048;
+                        const uint64_t ah = mn ? sdesc_mn_sw128(base + moff, A_BYTES / 2) : sdesc_k_sw128(base + off);
+                        const uint64_t al = mn ? sdesc_mn_sw128(base + A_BYTES + moff, A_BYTES / 2)
+                                               : sdesc_k_sw128(base + A_BYTES + off);
+                        const uint64_t bh = mn ? sdesc_mn_sw128(base + 2 * A_BYTES + moff, A_BYTES / 2)
+                                               : sdesc_k_sw128(base + 2 * A_BYTES + off);
+                        const uint64_t bl = mn ? sdesc_mn_sw128(base + 3 * A_BYTES + moff, A_BYTES / 2)
+                                               : sdesc_k_sw128(base + 3 * A_BYTES + off);
                         if (d.split_b) {  // hi(A) once from shared memory for hi.hi and hi.lo
-                            mma_bf16_pair_fill_a(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
-                            mma_bf16_pair_lastuse_a(dacc, ah, bl, idesc, 1u);
+                            mma_bf16_pair_fill_a(dacc, ah, bh, id, (kb == 0 && kk == 0) ? 0u : 1u);
+                            mma_bf16_pair_lastuse_a(dacc, ah, bl, id, 1u);
                         } else {
-                            mma_bf16_pair(dacc, ah, bh, idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                            mma_bf16_pair(dacc, ah, bh, id, (kb == 0 && kk == 0) ? 0u : 1u);
                         }
-                        mma_bf16_pair(dacc, al, bh, idesc, 1u);
+                        mma_bf16_pair(dacc, al, bh, id, 1u);
                     }
                     mma_commit_pair(&sy.empty[st]);
                 }
@@ -1502,10 +1517,8 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales)
         return e;
     const size_t TG = (size_t)d.Tp * d.Gp;
     // split copies of the current state (both W buffers get their maps; buffer 0 holds W now)
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < 2; ++b)
         k_split<<<1024, 256, 0, s>>>(d.W[b], TG, d.Wh[b], d.Wl[b]);
-        k_split<<<1024, 256, 0, s>>>(d.Wt[b], TG, d.Wth[b], d.Wtl[b]);
-    }
     k_split<<<1024, 256, 0, s>>>(d.Poff, (size_t)d.Tp * d.Tp, d.Ph, d.Pl);
     if (d.fp8) {  // scales from the state's norms (or as restored), then the E4M3 copies
         if (fresh_scales)
@@ -1546,8 +1559,8 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales)
         for (int b = 0; b < 2; ++b)
             if ((e = make_map(&m->Wh[b], d.Wh[b], d.Tp, d.Gp, 128)) ||
                 (e = make_map(&m->Wl[b], d.Wl[b], d.Tp, d.Gp, 128)) ||
-                (e = make_map(&m->Wth[b], d.Wth[b], d.Gp, d.Tp, 128)) ||
-                (e = make_map(&m->Wtl[b], d.Wtl[b], d.Gp, d.Tp, 128)))
+                (e = make_map(&m->Whm[b], d.Wh[b], d.Tp, d.Gp, 64)) ||
+                (e = make_map(&m->Wlm[b], d.Wl[b], d.Tp, d.Gp, 64)))
                 return e;
         int dev = 0, nsm = 0;
         if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))

@@ -164,8 +164,6 @@ int plan_memory(panda_ctx *c)
         for (int b = 0; b < 2; ++b) {
             DALLOC(d.Wh[b], Tp * Gp);
             DALLOC(d.Wl[b], Tp * Gp);
-            DALLOC(d.Wth[b], Gp * Tp);
-            DALLOC(d.Wtl[b], Gp * Tp);
         }
         DALLOC(d.Ph, Tp * Tp);
         DALLOC(d.Pl, Tp * Tp);

@@ -63,7 +63,7 @@ struct Dev {
     double *hist;                // HIST_CAP
     double *e2tab;               // HIST_CAP + 1: e^{2 alpha t}, computed on the host
     // BF16 split copies (tensor-core path only; NULL otherwise)
-    __nv_bfloat16 *Wh[2], *Wl[2], *Wth[2], *Wtl[2];
+    __nv_bfloat16 *Wh[2], *Wl[2];  // W^T operands are read from these MN-major
     __nv_bfloat16 *Ph, *Pl, *Ch, *Cl;
     // 1: B operands carry their lo halves too (BF16X3, hi.hi + hi.lo + lo.hi);
     // 0: B operands are BF16 hi only (BF16X2, hi.hi + lo.hi; C's lo half is never made)
