@@ -184,13 +184,6 @@ int plan_memory(panda_ctx *c)
     return 0;
 }
 
-int sync_ctl(panda_ctx *c)
-{
-    CU(cudaMemcpyAsync(c->h_ctl, c->d.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
-    CU(cudaStreamSynchronize(c->stream));
-    return 0;
-}
-
 int push_ctl(panda_ctx *c)
 {
     CU(cudaMemcpyAsync(c->d.ctl, c->h_ctl, sizeof(Ctl), cudaMemcpyHostToDevice, c->stream));
