@@ -161,6 +161,35 @@ def test_checkpoint_resume_is_bitwise(panda, prec):
     assert np.array_equal(ref_hist, hist)
 
 
+def test_checkpoint_from_another_context_is_rejected(panda):
+    """A checkpoint loads only into a context of the same shape, precision
+    and diagonal rule; a truncated or corrupted one is refused too, and the
+    context keeps working afterwards."""
+    W0, P0, C0 = gh.inputs("small64x256")
+    with panda.PandaContext(W0, P0, C0, prec=1) as a:
+        a.run(0.1, 0.0, 2)
+        blob = panda.panda_save(a.h)
+    others = [dict(prec=0), dict(prec=3), dict(prec=1, diag=2)]
+    for kw in others:
+        with panda.PandaContext(W0, P0, C0, **kw) as b:
+            with pytest.raises(panda.PandaError) as e:
+                panda.panda_load(b.h, blob)
+            assert e.value.code == -1
+            b.run(0.1, 0.0, 1)
+    W1, P1, C1 = W0[:, :200].copy(), P0, np.ascontiguousarray(C0[:200, :200])
+    with panda.PandaContext(W1, P1, C1, prec=1) as b:
+        with pytest.raises(panda.PandaError) as e:
+            panda.panda_load(b.h, blob)
+        assert e.value.code == -1
+    with panda.PandaContext(W0, P0, C0, prec=1) as b:
+        for bad in (blob[:-1], b"X" + blob[1:]):
+            with pytest.raises(panda.PandaError) as e:
+                panda.panda_load(b.h, bad)
+            assert e.value.code == -1
+        panda.panda_load(b.h, blob)  # the genuine one still loads
+        assert b.info()[3] == 2
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_set_state_continues_close(panda, prec):
     """A state read out and set into another context continues where the
