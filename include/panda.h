@@ -145,7 +145,12 @@ int panda_get_device(panda_ctx *ctx, float *dW, float *dP, float *dC);
  * C must be exactly symmetric and finite) and the counter; the derived
  * vectors (row and column norms, FP64 diagonals) are recomputed from them, so
  * a run continued from panda_set_state matches an uninterrupted one to FP32
- * rounding.  For a bit-exact resume use panda_save / panda_load. */
+ * rounding.  For a bit-exact resume use panda_save / panda_load.  When
+ * panda_set_state fails (for example PANDA_EASYM or PANDA_ENONFINITE on its
+ * input) the context's previous state is gone: step, run, get, save and
+ * batch runs then return PANDA_EINVAL until a panda_set_state or panda_load
+ * succeeds.  The same holds for a panda_load that fails after its header
+ * matched; one refused by the header check leaves the state untouched. */
 int panda_get_state(panda_ctx *ctx, float *W, float *P, float *C, int *t);
 int panda_set_state(panda_ctx *ctx, const float *W, const float *P, const float *C, int t);
 

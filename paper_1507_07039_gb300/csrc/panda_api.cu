@@ -23,6 +23,10 @@ struct panda_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int cur = 0;  // which W buffer holds the current network
+    // false once panda_set_state or panda_load has rejected its input or failed midway: the
+    // device then holds no valid state, and everything that reads it refuses until one of
+    // them succeeds
+    bool state_ok = true;
     Dev d{};
     Ctl *h_ctl = nullptr;  // pinned mirror of the device control block
     std::vector<void *> allocs;
@@ -433,6 +437,14 @@ int drive(panda_ctx *c, float alpha, double tol, int max_iter, bool use_graph, i
 
 int check_ctx(const panda_ctx *c) { return c ? 0 : PANDA_EINVAL; }
 
+int check_state(panda_ctx *c)
+{
+    return c->state_ok ? 0
+                       : set_err(c, PANDA_EINVAL,
+                                 "the context holds no valid state (a panda_set_state or panda_load failed): "
+                                 "give it one with panda_set_state or panda_load");
+}
+
 void free_all(panda_ctx *c)
 {
     if (!c)
@@ -670,6 +682,8 @@ int panda_step(panda_ctx *c, float alpha, double *h_out)
     Range r("panda_step");
     if (check_ctx(c))
         return PANDA_EINVAL;
+    if (int rc = check_state(c))
+        return rc;
     if (!(alpha >= 0.0f && alpha <= 1.0f))
         return set_err(c, PANDA_EINVAL, "alpha must be in [0, 1]");
     int n = 0;
@@ -686,6 +700,8 @@ int panda_run(panda_ctx *c, float alpha, double tol, int max_iter, int *iters_ou
     Range r("panda_run");
     if (check_ctx(c))
         return PANDA_EINVAL;
+    if (int rc = check_state(c))
+        return rc;
     if (!(alpha >= 0.0f && alpha <= 1.0f))
         return set_err(c, PANDA_EINVAL, "alpha must be in [0, 1]");
     if (!(tol >= 0.0) || max_iter < 0)
@@ -713,6 +729,8 @@ static int full_matrices(panda_ctx *c)
 
 static int get_impl(panda_ctx *c, float *W, float *P, float *C)
 {
+    if (int rc = check_state(c))
+        return rc;
     Dev &d = c->d;
     if ((P || C) && full_matrices(c))
         return PANDA_ECUDA;
@@ -778,6 +796,7 @@ int panda_set_state(panda_ctx *c, const float *W, const float *P, const float *C
     drop_graphs(c);
     Dev &d = c->d;
     c->cur = 0;
+    c->state_ok = false;  // until the new networks are in, validated and their vectors derived
     int rc;
     if ((rc = upload(c, d.W[0], c->Gp, W, c->T, c->G)) || (rc = upload(c, d.Poff, c->Tp, P, c->T, c->T)) ||
         (rc = upload(c, d.Coff, c->Gp, C, c->G, c->G)))
@@ -790,6 +809,7 @@ int panda_set_state(panda_ctx *c, const float *W, const float *P, const float *C
     if ((rc = push_ctl(c)))
         return rc;
     CU(cudaStreamSynchronize(c->stream));
+    c->state_ok = true;
     return 0;
 }
 
@@ -836,6 +856,8 @@ int panda_save(panda_ctx *c, void *buf, long long bytes)
 {
     if (check_ctx(c))
         return PANDA_EINVAL;
+    if (int rc = check_state(c))
+        return rc;
     if (!buf || bytes < panda_checkpoint_bytes(c))
         return set_err(c, PANDA_EINVAL, "checkpoint buffer too small");
     CkptHeader h{};
@@ -866,6 +888,7 @@ int panda_load(panda_ctx *c, const void *buf, long long bytes)
         h.prec != c->prec || h.diag != c->diag)
         return set_err(c, PANDA_EINVAL, "checkpoint does not match this context");
     drop_graphs(c);
+    c->state_ok = false;  // until every item is back
     const char *p = static_cast<const char *>(buf) + sizeof h;
     for (auto &it : ckpt_items(c)) {
         CU(cudaMemcpyAsync(it.dev, p, it.bytes, cudaMemcpyHostToDevice, c->stream));
@@ -884,6 +907,7 @@ int panda_load(panda_ctx *c, const void *buf, long long bytes)
     if (rc)
         return rc;
     CU(cudaStreamSynchronize(c->stream));
+    c->state_ok = true;
     return 0;
 }
 
@@ -1215,6 +1239,11 @@ int panda_batch_run(panda_batch *b, float alpha, double tol, int max_iter, int *
         b->err = "alpha must be in [0, 1], tol >= 0 and max_iter >= 0";
         return PANDA_EINVAL;
     }
+    for (size_t k = 0; k < b->nets.size(); ++k)
+        if (int rc = check_state(b->nets[k])) {
+            b->err = "network " + std::to_string(k) + ": " + b->nets[k]->err;
+            return rc;
+        }
     if (b->set)
         return batch_run_set(b, alpha, tol, max_iter, iters_out, h_last);
     const size_t n = b->nets.size();

@@ -208,6 +208,29 @@ def test_set_state_continues_close(panda, prec):
     assert np.max(np.abs(ref[0] - got[0])) < (1e-5 if prec == 0 else 1e-4)
 
 
+def test_rejected_state_blocks_the_context_until_a_valid_one(panda):
+    """panda_set_state with an asymmetric C is refused (EASYM); the context
+    then refuses to step, run, get or save (EINVAL) instead of iterating on
+    networks it has not validated, until a valid state is set."""
+    W0, P0, C0 = gh.inputs("small64x256")
+    with panda.PandaContext(W0, P0, C0, prec=1) as ctx:
+        ctx.run(0.1, 0.0, 2)
+        W, P, C, t = panda.panda_get_state(ctx.h, 64, 256)
+        bad = C.copy()
+        bad[3, 9] += 1.0
+        with pytest.raises(panda.PandaError) as e:
+            panda.panda_set_state(ctx.h, W, P, bad, t)
+        assert e.value.code == -5
+        for call in (lambda: ctx.step(0.1), lambda: ctx.run(0.1, 0.0, 2), lambda: ctx.get(),
+                     lambda: panda.panda_save(ctx.h)):
+            with pytest.raises(panda.PandaError) as e:
+                call()
+            assert e.value.code == -1 and "no valid state" in str(e.value)
+        panda.panda_set_state(ctx.h, W, P, C, t)
+        ctx.step(0.1)
+        assert ctx.info()[3] == t + 1
+
+
 @pytest.mark.parametrize("prec", [0, 1, 3])
 def test_device_pointer_create_matches_host(panda, prec):
     """panda_create_device on torch-owned buffers and panda_get_device into
