@@ -2,14 +2,16 @@
 // every GEMM tile on a CTA pair (cta_group::2, 256 x 256 outputs).
 //
 //   k_tc_phase1   per 256 (TFs) x 256 (genes) tile of W': two TMEM accumulators,
-//                   R-num = P_off . W   (K = TFs;   A = P_off rows, B = W^T rows)
+//                   R-num = P_off . W   (K = TFs;   A = P_off rows, B = W columns)
 //                   A-num = W . C_off   (K = genes; A = W rows,     B = C_off rows)
 //                 then the fused epilogue of Eqs. 1-3 and 2: diagonal terms,
 //                 Tanimoto, damped W update, h and norm partials, and the
-//                 FP32 W' plus its split copies in both orientations.
+//                 FP32 W' plus its split copy (under FP8MIX also E4M3 copies
+//                 of W' and W'^T).
 //   k_reduce_wnorms  (shared with the FP32 path)
 //   k_tc_phase2   persistent: upper-triangle 256 x 256 tiles of W'.W'^T (P,
-//                 K = genes) and W'^T.W' (C, K = TFs) from a balanced host-built
+//                 K = genes) and W'^T.W' (C, K = TFs; columns of W' as both
+//                 operands) from a balanced host-built
 //                 schedule, double-buffered TMEM accumulators, and the Eq. 5
 //                 epilogue: Tanimoto, damped update, the FP32 upper triangle,
 //                 split copies of the upper triangle (of P: both triangles; of
@@ -24,6 +26,9 @@
 // (upper triangle and diagonal blocks), and as C_off[k][j], rows k of the
 // upper triangle loaded MN-major, where k lies before it: the split copy of
 // C's lower triangle outside the diagonal blocks is never written or read.
+// W is kept in one orientation: where a product needs columns of W (B of
+// R-num, both operands of the C tiles) they are rows k of W's split copy,
+// loaded as 64 x 64 boxes and fed to the MMAs MN-major.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -471,8 +476,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 // ---------------------------------------------------------------------------
 // Phase 1 on CTA pairs: one 256 (TFs) x 256 (genes) tile of W' per pair
 // (grid x = 2 x T tiles, y = G tiles).  CTA r loads rows 128 r .. + 127 of
-// the tile's A blocks (P_off for R, W for A) and of its B blocks (W^T for R,
-// C_off for A); the even CTA issues cta_group::2 MMAs into two TMEM
+// the tile's A blocks (P_off for R, W for A) and of its B blocks (columns of W
+// for R, C_off for A); the even CTA issues cta_group::2 MMAs into two TMEM
 // accumulators of 256 columns (R at column 0, A at column 256).  Warps:
 // 0 TMA, 1 MMA (even CTA), 2-9 epilogue (two per TMEM lane quarter, each
 // taking 128 of the 256 columns in 16-column sub-chunks).
