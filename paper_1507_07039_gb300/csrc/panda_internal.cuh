@@ -1,10 +1,13 @@
 // Internal declarations of libpanda_gb300 (not part of the C ABI).
 //
 // Device layout (all row-major, every dimension padded with zeros to a
-// multiple of 128 so that GEMM tiles never need bounds checks in their main
-// loops; the epilogues mask by the true T and G):
+// multiple of 128, or 256 on the tensor-core path, so that GEMM tiles never
+// need bounds checks in their main loops; the epilogues mask by the true T
+// and G):
 //   W[2]   Tp x Gp  fp32   regulatory network, ping-pong (current / next)
-//   Wt[2]  Gp x Tp  fp32   its transpose, written by the same epilogue
+//   Wt[2]  Gp x Tp  fp32   its transpose: written by the FP32 path's epilogue;
+//                          on the tensor-core path made at create and load only
+//                          (column norms, FP8MIX's E4M3 copy)
 //   Poff   Tp x Tp  fp32   P with a zero diagonal (diagonal kept in pd)
 //   Coff   Gp x Gp  fp32   C with a zero diagonal (diagonal kept in cd)
 //   pd, cd          fp64   diagonals of P and C
