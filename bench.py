@@ -601,8 +601,9 @@ def main(argv=None):
     ap.add_argument("--ref-frac", type=float, default=0.02)
     ap.add_argument("--table-reps", type=int, default=16, help="networks per size in --workload table1")
     args = ap.parse_args(argv)
-    if args.warmup < 3:
-        ap.error("--warmup must be at least 3")
+    if args.warmup < 3:  # the timing rules want at least 3; the line reports what ran
+        print(f"bench.py: --warmup {args.warmup} raised to 3", file=sys.stderr)
+        args.warmup = 3
     rank, world, local_rank = dist_env()
     wl = synth.get(args.workload) if args.workload not in ("set64", "table1") else None
     if args.impl == "reference":
