@@ -140,7 +140,8 @@ int panda_get(panda_ctx *ctx, float *W, float *P, float *C);
  * complete when the call returns. */
 int panda_get_device(panda_ctx *ctx, float *dW, float *dP, float *dC);
 
-/* Networks plus the number of iterations done so far (*t, may be NULL).
+/* Networks plus the number of iterations done so far (*t, may be NULL); the
+ * buffers may be host or device memory (of the context's device).
  * panda_set_state replaces the networks (taken as already normalised; P and
  * C must be exactly symmetric and finite) and the counter; the derived
  * vectors (row and column norms, FP64 diagonals) are recomputed from them, so

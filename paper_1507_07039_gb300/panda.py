@@ -210,6 +210,14 @@ def panda_set_state(ctx, W, P, C, t):
     _check(lib.panda_set_state(ctx, _ptr(W), _ptr(P), _ptr(C), int(t)), ctx)
 
 
+def panda_set_state_device(ctx, dW, dP, dC, t):
+    """panda_set_state from device buffers (torch CUDA tensors or raw pointers
+    of this device)."""
+    def ptr(x):
+        return ctypes.c_void_p(x if isinstance(x, int) else x.data_ptr())
+    _check(lib.panda_set_state(ctx, ptr(dW), ptr(dP), ptr(dC), int(t)), ctx)
+
+
 def panda_save(ctx) -> bytes:
     n = lib.panda_checkpoint_bytes(ctx)
     buf = ctypes.create_string_buffer(n)
