@@ -283,6 +283,10 @@ def run_reference(args, wl, rank, world):
 # measurements are made of segments of at most SEG iterations, each restarted
 # from the Z-scored start state at t = 0.
 SEG = 100
+# Networks of a set with few TFs and many genes reach that limit first: after
+# 66-70 iterations for T ~ 240-300, G ~ 15000-17000 (measured over set64);
+# a set's warm-up plus one segment stays within 60.
+SEG_SET = 40
 
 
 def segments(n: int) -> list[int]:
@@ -537,25 +541,36 @@ def run_set(args, rank, world, local_rank):
     flops = sum(algorithmic_flops(w.T, w.G) for w in wls)
     # warm-up: at least the phase-2 schedule trials of the tensor-core set engine (one iteration
     # each, plus one) and one captured chunk, so that neither falls in the timed region
-    warm = max(args.warmup, 16) if prec != panda.PANDA_FP32 else args.warmup
-    with panda.PandaBatch(nets, prec=prec) as b:
-        del nets
-        b.run(ALPHA, 0.0, warm)
-        clocks = ClockSampler(gpu_id_for(local_rank)) if rank == 0 else None
-        torch.cuda.synchronize()
-        if clocks:
-            clocks.start()
-            time.sleep(0.6)
-        barrier(world)
-        t0 = time.perf_counter()
-        conv, iters, _ = b.run(ALPHA, 0.0, args.steps)
-        torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
-        barrier(world)
-        sec = max_over_ranks(sec, world, torch.device("cuda", local_rank))  # replicas: the slowest rank
-        ck = clocks.stop() if clocks else None
-        sched = b.schedule()
-    assert all(i == args.steps for i in iters)
+    warm = min(max(args.warmup, 16) if prec != panda.PANDA_FP32 else args.warmup, 20)
+    # the diagonals' e^{2 alpha t} growth (see SEG): more than SEG_SET timed iterations run as
+    # segments, each on a freshly created set with its own warm-up, the creation untimed
+    seg_set = min(SEG_SET, 60 - warm)
+    segs = []
+    left = args.steps
+    while left > 0:
+        segs.append(min(seg_set, left))
+        left -= segs[-1]
+    clocks = ClockSampler(gpu_id_for(local_rank)) if rank == 0 else None
+    sec, sched = 0.0, None
+    for q, n in enumerate(segs):
+        with panda.PandaBatch(nets, prec=prec) as b:
+            if q == len(segs) - 1:
+                del nets
+            b.run(ALPHA, 0.0, warm)
+            torch.cuda.synchronize()
+            if clocks and q == 0:
+                clocks.start()
+                time.sleep(0.6)
+            barrier(world)
+            t0 = time.perf_counter()
+            conv, iters, _ = b.run(ALPHA, 0.0, n)
+            torch.cuda.synchronize()
+            sec += time.perf_counter() - t0
+            barrier(world)
+            sched = b.schedule()
+        assert all(i == n for i in iters)
+    sec = max_over_ranks(sec, world, torch.device("cuda", local_rank))  # replicas: the slowest rank
+    ck = clocks.stop() if clocks else None
     value = world * len(wls) * args.steps / sec  # the whole job: every rank iterates its own copy of the set
     if rank == 0:
         print(json.dumps({
