@@ -297,6 +297,12 @@ def segments(n: int) -> list[int]:
     return out
 
 
+def launched_iterations(steps: int) -> int:
+    """Iterations whose kernels the timed graphs launch: whole graphs per
+    segment (those past a segment's last iteration return at once)."""
+    return sum(-(-n // GRAPH_ITERS) * GRAPH_ITERS for n in segments(steps))
+
+
 def start_state(panda, torch, ctx, T, G, device):
     """The context's networks at t = 0, kept on the device for restarts."""
     st = [torch.empty(s, dtype=torch.float32, device=device) for s in ((T, G), (T, T), (G, G))]
@@ -496,7 +502,7 @@ def run_ours(args, wl, rank, world, local_rank):
 
     # each captured graph launches the kernels of all its iterations; those past the run's last
     # iteration return at once, so the launches are whole graphs' worth, the work is `steps`' worth
-    launches = sum(-(-n // GRAPH_ITERS) * GRAPH_ITERS for n in segments(args.steps)) * len(kstats)
+    launches = launched_iterations(args.steps) * len(kstats)
     launches_with_work = int(sum(k[2] for k in kstats))
     if rank == 0:
         line = {
