@@ -197,6 +197,92 @@ def traffic_for(kernel: str, workload: str) -> float | None:
     return float(rec["bytes_per_launch"]) if sha == rec["source_sha"] else None
 
 
+def tensor_peak(peaks: dict, peak_src: str, ck: dict | None, timed_ms: float) -> tuple[float, str]:
+    """The BF16 dense peak that applies to a kernel timed inside the bench's
+    timed region: the burst figure when that region ran at the maximum SM
+    clock and lasted under a second, else the sustained (power-capped) one."""
+    burst = peaks.get("bf16_tflops", FALLBACK["bf16_tflops"])
+    sustained = peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
+    mx = (ck or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    sm = (ck or {}).get("sm_mhz")
+    if sm is not None and sm >= 0.97 * mx and timed_ms < 1000.0:
+        return burst, (f"bf16 dense burst ({peak_src}): the timed region lasted {timed_ms:.0f} ms "
+                       f"at a median {sm:.0f} MHz of {mx:.0f}")
+    why = "no clock record" if sm is None else f"median {sm:.0f} MHz, {timed_ms:.0f} ms timed"
+    return sustained, f"bf16 dense sustained ({peak_src}; {why})"
+
+
+def kernel_flops(panda, prec: int, name: str, T: int, G: int) -> tuple[float, float, float]:
+    """(useful flops, issued tensor flops, issued flops in BF16-MMA time
+    units) of one launch of a tensor-core kernel: BF16X3 issues three MMAs per
+    product, BF16X2 two; FP8MIX runs the gene-sized products as one E4M3 MMA,
+    which takes half the time of a BF16 one, and the TF-sized ones as BF16X3."""
+    useful = kernel_algorithmic_work(name, T, G)[0]
+    big, small = kernel_split_work(name, T, G)
+    if prec == panda.PANDA_FP8MIX:
+        return useful, big + 3.0 * small, 0.5 * big + 3.0 * small
+    terms = 3.0 if prec == panda.PANDA_BF16X3 else 2.0
+    return useful, terms * useful, terms * useful
+
+
+def roofline(panda, prec, kstats, T, G, wl_name, peaks, peak_src, ck, timed_ms, ffma, iters_per_s):
+    """The bench line's roofline object: the dominant kernel against the peak
+    of its pipe, every product kernel beside it, and the whole iteration."""
+    top = max(kstats, key=lambda k: k[1])
+    work, _ = kernel_algorithmic_work(top[0], T, G)
+    avg_s = top[1] / top[2] / 1000.0
+    hbm = peaks.get("hbm_gbs", FALLBACK["hbm_gbs"])
+    if prec == panda.PANDA_FP32:
+        if ffma:
+            peak, src = ffma, "FP32 FFMA loop on every SM, timed by CUDA events on this GPU (measured)"
+        else:
+            peak = SMS * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            src = (f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
+                   f"(nominal, {peak_src} max clock)")
+        roof = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "peak_source": src}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+        roof["kernel"] = top[0]
+        roof["traffic"] = traffic_for(top[0], wl_name)
+        return roof
+    bf16, src = tensor_peak(peaks, peak_src, ck, timed_ms)
+    fp8 = prec == panda.PANDA_FP8MIX
+    peak = 2.0 * bf16 if fp8 else bf16
+    if fp8:
+        src = "e4m3 dense = 2 x " + src + " (nominal ratio)"
+    per_kernel = []
+    issued_units_iter = 0.0
+    for name, ms_tot, launches in kstats:
+        useful, issued, units = kernel_flops(panda, prec, name, T, G)
+        if not useful or not launches:
+            continue
+        t = ms_tot / launches / 1000.0
+        traffic = traffic_for(name, wl_name)
+        per_kernel.append({
+            "kernel": name, "ms_avg": round(1000.0 * t, 5),
+            "useful_tflops": useful / t / 1e12, "issued_tensor_tflops": issued / t / 1e12,
+            "useful_frac": useful / t / 1e12 / peak,
+            # issued MMAs against the BF16 peak (E4M3 MMAs counted at half a BF16 MMA's time)
+            "issued_frac": units / t / 1e12 / bf16,
+            "traffic": traffic, "hbm_gbs": None if traffic is None else traffic / t / 1e9,
+            "hbm_frac": None if traffic is None else traffic / t / 1e9 / hbm})
+        issued_units_iter += units
+    useful_iter = algorithmic_flops(T, G)
+    roof = {"bound": "tensor", "achieved": work / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "peak_source": src, "kernel": top[0],
+            "issued_tensor_tflops": kernel_flops(panda, prec, top[0], T, G)[1] / avg_s / 1e12}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = traffic_for(top[0], wl_name)
+    roof["kernels"] = per_kernel
+    roof["iteration"] = {
+        "useful_tflops": useful_iter * iters_per_s / 1e12,
+        "useful_frac": useful_iter * iters_per_s / 1e12 / peak,
+        "issued_frac": issued_units_iter * iters_per_s / 1e12 / bf16,
+        "note": "useful = 3TG^2 + 3T^2G flop per iteration; issued counts every MMA the split issues"}
+    roof["hbm_peak_gbs"] = hbm
+    return roof
+
+
 # ---------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle on a bounded sample of one iteration
 # ---------------------------------------------------------------------------
@@ -240,6 +326,41 @@ def cpu_threads() -> int:
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def accuracy_sample(panda, s, W0, P0, C0, prec, n_rows: int = 100) -> dict:
+    """Errors of the first iteration against the FP64 oracle, for the metric's
+    gate: rows of W' (the oracle's own Eqs. 2-4 on the rows the CPU sample
+    computed), and whole rows of P' and C' with their diagonals (the oracle's
+    Eqs. 5-6 given the GPU's W', widened to FP64: W' differs from the oracle's
+    by about 1e-5, which moves a P' or C' entry by about 1e-6 of its scale, far
+    below the step's own error).  Off-diagonal errors are relative to the row's
+    largest entry (at least 1), diagonal errors relative to the entry."""
+    with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:
+        ctx.step(ALPHA)
+        gW, gP, gC = ctx.get()
+    orc, a = s.orc, float(np.float32(ALPHA))
+    T, G = gW.shape
+    errW = float(np.max(np.abs(gW[s.rows].astype(np.float64) - s.w_rows)))
+    Wn = gW.astype(np.float64)
+    rng = np.random.default_rng(11)
+    out = {"W": errW}
+    for name, X, gX, rows_of, mult, n in (("P", s.P, gP, orc.p_rows, G, T), ("C", s.C, gC, orc.c_rows, T, G)):
+        rows = np.sort(rng.choice(n, min(n_rows, n), replace=False))
+        o = rows_of(Wn, X, a, rows)
+        eo, ed = 0.0, 0.0
+        for q, i in enumerate(rows):
+            off = np.arange(n) != i
+            scale = max(1.0, float(np.max(np.abs(o[q][off])))) if n > 1 else 1.0
+            if n > 1:
+                eo = max(eo, float(np.max(np.abs(gX[i][off] - o[q][off]))) / scale)
+            d = orc.diag_value(o[q], i, mult, X[i, i], a, 1)
+            ed = max(ed, abs(float(gX[i, i]) - d) / max(1.0, abs(d)))
+        out[name + "off"], out[name + "diag"] = eo, ed
+    return {"max_abs_dW_vs_fp64_oracle": errW, "errors": out, "gate": 1e-4, "within_gate": errW <= 1e-4,
+            "iteration": 1, "W_rows": int(len(s.rows)), "P_rows": min(n_rows, T), "C_rows": min(n_rows, G),
+            "of": [T, G], "P_C_reference": "oracle Eqs. 5-6 applied to the GPU's W' (FP64-widened)",
+            "trajectory_errors": "whole converging runs at T = 1000 are checked by the GPU tests"}
 
 
 # ---------------------------------------------------------------------------
@@ -357,14 +478,28 @@ def time_gpu(panda, torch, W0, P0, C0, prec, steps, warmup, world, local_rank, w
     return ms, kstats, ck
 
 
-def run_segments(panda, torch, ctx, steps, T, G, device):
-    """steps iterations, restarted from the start state every SEG iterations."""
+def run_segments(panda, torch, ctx, steps, T, G, device) -> float:
+    """steps iterations, restarted from the start state every SEG iterations.
+    Returns the seconds spent on the restarts (the start-state snapshot and
+    each panda_set_state_device, timed between device syncs): bench-only work
+    that the end-to-end figure leaves out."""
     segs = segments(steps)
-    st = start_state(panda, torch, ctx, T, G, device) if len(segs) > 1 else None
+    overhead = 0.0
+    st = None
+    if len(segs) > 1:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = start_state(panda, torch, ctx, T, G, device)
+        overhead += time.perf_counter() - t0
     for k, n in enumerate(segs):
         if k:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             panda.panda_set_state_device(ctx.h, *st, 0)
+            torch.cuda.synchronize()
+            overhead += time.perf_counter() - t0
         ctx.run(ALPHA, 0.0, n)
+    return overhead
 
 
 def time_e2e(panda, torch, W0, P0, C0, prec, steps):
@@ -379,11 +514,11 @@ def time_e2e(panda, torch, W0, P0, C0, prec, steps):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     ctx = panda.PandaContext(*pin, prec=prec)
-    run_segments(panda, torch, ctx, steps, T, G, device)
+    restarts = run_segments(panda, torch, ctx, steps, T, G, device)
     panda.panda_get_into(ctx.h, *outs)
     t1 = time.perf_counter()
     ctx.close()
-    return t1 - t0, sum(x.nbytes for x in pin) / steps, sum(x.nbytes for x in outs) / steps
+    return t1 - t0 - restarts, sum(x.nbytes for x in pin) / steps, sum(x.nbytes for x in outs) / steps
 
 
 def time_e2e_expression(panda, torch, wl, prec, steps):
@@ -400,11 +535,11 @@ def time_e2e_expression(panda, torch, wl, prec, steps):
     t0 = time.perf_counter()
     ctx = panda.PandaContext.from_expression(*pin, prec=prec)
     t1 = time.perf_counter()
-    run_segments(panda, torch, ctx, steps, T, G, torch.device("cuda", torch.cuda.current_device()))
+    restarts = run_segments(panda, torch, ctx, steps, T, G, torch.device("cuda", torch.cuda.current_device()))
     panda.panda_get_into(ctx.h, *outs)
     t2 = time.perf_counter()
     ctx.close()
-    return t2 - t0, t1 - t0, sum(x.nbytes for x in pin) / steps, sum(x.nbytes for x in outs) / steps
+    return t2 - t0 - restarts, t1 - t0, sum(x.nbytes for x in pin) / steps, sum(x.nbytes for x in outs) / steps
 
 
 def run_ours(args, wl, rank, world, local_rank):
@@ -440,28 +575,13 @@ def run_ours(args, wl, rank, world, local_rank):
     kernels = {k[0]: {"launches": k[2], "ms_total": round(k[1], 4),
                       "ms_avg": round(k[1] / k[2], 5) if k[2] else None, "share": round(k[1] / tot, 4)}
                for k in kstats}
-    top = max(kstats, key=lambda k: k[1])
-    work, _ = kernel_algorithmic_work(top[0], T, G)
-    avg_s = top[1] / top[2] / 1000.0
-    if prec == panda.PANDA_FP32:
-        peak = SMS * FP32_LANES * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": work / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"FP32 FFMA: 152 SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz ({peak_src} max clock)"}
-    elif prec == panda.PANDA_FP8MIX:
-        # the gene-sized products run on E4M3 (one term), the TF-sized ones on BF16X3
-        peak = 2.0 * peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
-        big, small = kernel_split_work(top[0], T, G)
-        roof = {"bound": "tensor", "achieved": work / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"e4m3 dense = 2 x bf16 dense sustained ({peak_src} bf16 x nominal ratio)",
-                "issued_tensor_tflops": (big + 3.0 * small) / avg_s / 1e12}
-    else:
-        peak = peaks.get("bf16_tflops_sustained", FALLBACK["bf16_tflops_sustained"])
-        roof = {"bound": "tensor", "achieved": work / avg_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"bf16 dense sustained ({peak_src})",
-                "issued_tensor_tflops": (3.0 if prec == panda.PANDA_BF16X3 else 2.0) * work / avg_s / 1e12}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["kernel"] = top[0]
-    roof["traffic"] = traffic_for(top[0], wl.name)
+    ffma = None
+    try:
+        ffma = panda.panda_measure_ffma_peak()
+    except panda.PandaError:
+        pass
+    roof = roofline(panda, prec, kstats, T, G, wl.name, peaks, peak_src, ck, ms, ffma,
+                    value / world)
 
     e2e = None
     if args.e2e:
@@ -470,7 +590,9 @@ def run_ours(args, wl, rank, world, local_rank):
         e2e = {"value": world * args.steps / sec,
                "unit": "iterations/s", "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                "note": "create from pinned host buffers (H2D + validation + Z-score), the iterations, "
-                       "read-back of W, P, C (D2H); per-step bytes = totals / steps"}
+                       "read-back of W, P, C (D2H); per-step bytes = totals / steps; runs of more than "
+                       f"{SEG} steps restart from the start state every {SEG} iterations (the diagonals' "
+                       "e^(2 alpha t) growth) and leave those restarts out of the time"}
         if wl.n_samples > 0:  # the same from expression data: C0 computed on the GPU (Pearson, Sec. II-A)
             sec2, create2, bi2, bo2 = time_e2e_expression(panda, torch, wl, prec, args.steps)
             sec2 = max_over_ranks(sec2, world, torch.device("cuda", local_rank))
@@ -492,13 +614,7 @@ def run_ours(args, wl, rank, world, local_rank):
                "sample": f"fraction {args.cpu_frac} of one iteration ({max(1, round(args.cpu_frac * T))} rows "
                          f"of W' and of P', {max(1, round(args.cpu_frac * G))} rows of C'), "
                          f"{el:.1f} s of CPU time, scaled to a full iteration"}
-        # the same rows of the first iteration's W' on the GPU, against the oracle's (the metric's gate)
-        with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:
-            ctx.step(ALPHA)
-            gW = ctx.get(want=(True, False, False))[0]
-        err = float(np.max(np.abs(gW[s.rows].astype(np.float64) - s.w_rows)))
-        accuracy = {"max_abs_dW_vs_fp64_oracle": err, "rows": int(len(s.rows)), "of": T, "iteration": 1,
-                    "gate": 1e-4, "within_gate": err <= 1e-4}
+        accuracy = accuracy_sample(panda, s, W0, P0, C0, prec)
 
     # each captured graph launches the kernels of all its iterations; those past the run's last
     # iteration return at once, so the launches are whole graphs' worth, the work is `steps`' worth
@@ -524,6 +640,7 @@ def run_ours(args, wl, rank, world, local_rank):
             "gpu_launches_with_work": launches_with_work,
             "clocks": ck,
             "kernels": kernels,
+            "fp32_ffma_peak_tflops": ffma,
         }
         if other:
             line.update(other)

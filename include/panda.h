@@ -202,6 +202,15 @@ int panda_kernel_stats(const panda_ctx *ctx, int i, char *name, int name_cap, do
  * other terms or non-positive sizes; PANDA_EUNSUPPORTED off sm_103. */
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms);
 
+/* Measurement support (no paper counterpart): the FP32 fused multiply-add
+ * throughput of the current device, the roof of the FP32 path's products.
+ * A loop of independent FMAs (8 chains per thread, 16 warps per scheduler) runs
+ * on every SM; the best of ten launches timed by CUDA events after two
+ * warm-up launches gives *tflops (FP32 TFLOP/s, 2 flop per FMA).  Allocates
+ * and frees a few bytes of device memory.  PANDA_EINVAL for NULL,
+ * PANDA_ECUDA when a CUDA call fails. */
+int panda_measure_ffma_peak(double *tflops);
+
 /* Test of the bounded device waits (no paper counterpart): runs the
  * tensor-core self-test product with one pipeline stage armed but never
  * loaded, so its barrier never completes; the kernel's bounded waits give up
@@ -284,17 +293,21 @@ void panda_batch_destroy(panda_batch *b);
  * They are used as given: no Z-score is applied (normalise them first, or
  * take them from panda_get).  dP and dC must be exactly symmetric
  * (PANDA_EASYM) and finite (PANDA_ENONFINITE).  alpha in [0, 1]; t >= 1 is
- * the 1-based iteration index used in the e^{2 alpha t} factor of Eq. 6;
- * diag is a panda_diag rule.  *h_out (may be NULL) receives h.  The call
- * runs on `stream` (a cudaStream_t, NULL = legacy default stream) and blocks
- * until the iteration is done.
+ * the 1-based iteration index used in the diagonal growth factor
+ * e^{2 alpha t}; diag is a panda_diag rule.  *h_out (may be NULL) receives
+ * h.  The call runs on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and blocks until the iteration is done.  When it returns an error
+ * (PANDA_ENONFINITE included) dW, dP and dC hold what they held before.
  *
  * Working memory is one file-scope device array of about 7.4 MB, sized for
  * T, G <= PANDA_STATIC_MAX_NODES; larger shapes are rejected with
- * PANDA_EINVAL before any GPU work.  Every GPU that loads the library holds
- * the array until the process exits.  The first call on each device looks up
- * the array's device address (with that device current); make that first
- * call before any stream capture.  All calls share the array and clear it at
+ * PANDA_EINVAL before any GPU work.  Every GPU that loads the library's
+ * device code holds the array until the process exits; with CUDA's lazy
+ * module loading (the default) that happens at the first call on the
+ * device, so a caller with a fixed memory budget makes that call at
+ * start-up.  The first call on each device also looks up the array's device
+ * address (with that device current); make that first call before any
+ * stream capture.  All calls share the array and clear it at
  * their start, so calls that overlap on the GPU (for example on two streams)
  * race and must be serialised by the caller.  Errors are reported by the
  * return code and panda_last_error(NULL). */

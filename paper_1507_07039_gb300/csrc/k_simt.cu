@@ -618,3 +618,75 @@ cudaError_t launch_iteration_simt(const Dev &d, int cur, cudaStream_t s, KernelE
 }
 
 }  // namespace panda
+
+// ---- FP32 FFMA throughput of the device (measurement support) -------------
+namespace panda {
+namespace {
+
+constexpr int FFMA_CHAINS = 8, FFMA_LOOP = 2048, FFMA_THREADS = 512;
+
+// Every thread runs FFMA_CHAINS independent chains x <- x * a + b for
+// FFMA_LOOP rounds (a, b are launch arguments, so nothing is folded); the
+// store is taken only if a chain lands on `never`, which the host makes
+// unreachable, so the loop is not removed.
+__global__ void __launch_bounds__(FFMA_THREADS) k_ffma_loop(float a, float b, float never, float *out)
+{
+    float x[FFMA_CHAINS];
+#pragma unroll
+    for (int c = 0; c < FFMA_CHAINS; ++c)
+        x[c] = (float)(threadIdx.x + c) * 1e-3f;
+#pragma unroll 4
+    for (int it = 0; it < FFMA_LOOP; ++it)
+#pragma unroll
+        for (int c = 0; c < FFMA_CHAINS; ++c)
+            x[c] = fmaf(x[c], a, b);
+    float s = 0.0f;
+#pragma unroll
+    for (int c = 0; c < FFMA_CHAINS; ++c)
+        s += x[c];
+    if (s == never)
+        out[blockIdx.x] = s;
+}
+
+}  // namespace
+
+cudaError_t measure_ffma_peak(double *tflops)
+{
+    int dev = 0, nsm = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
+        return e;
+    float *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if ((e = cudaMalloc(&out, sizeof(float) * 4 * nsm)))
+        return e;
+    const int blocks = 4 * nsm;  // 4 x 16 warps per SM: 16 per scheduler
+    double best_ms = 1e30;
+    if (!(e = cudaEventCreate(&e0)) && !(e = cudaEventCreate(&e1))) {
+        for (int rep = 0; rep < 12 && !e; ++rep) {
+            cudaEventRecord(e0);
+            k_ffma_loop<<<blocks, FFMA_THREADS>>>(0.999f, 1e-4f, -1.0f, out);
+            cudaEventRecord(e1);
+            if (!(e = cudaEventSynchronize(e1))) {
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep >= 2 && ms < best_ms)  // the first launches warm up the clocks
+                    best_ms = ms;
+            }
+        }
+        if (!e)
+            e = cudaGetLastError();
+    }
+    if (e0)
+        cudaEventDestroy(e0);
+    if (e1)
+        cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e)
+        return e;
+    const double flop = 2.0 * FFMA_CHAINS * FFMA_LOOP * (double)FFMA_THREADS * blocks;
+    *tflops = flop / (best_ms * 1e-3) / 1e12;
+    return cudaSuccess;
+}
+
+}  // namespace panda

@@ -972,6 +972,16 @@ int panda_selftest_timeout(void)
     return 0;
 }
 
+int panda_measure_ffma_peak(double *tflops)
+{
+    if (!tflops)
+        return set_err(nullptr, PANDA_EINVAL, "panda_measure_ffma_peak: NULL output");
+    cudaError_t e = measure_ffma_peak(tflops);
+    if (e != cudaSuccess)
+        return set_err(nullptr, PANDA_ECUDA, std::string("panda_measure_ffma_peak: ") + cudaGetErrorString(e));
+    return 0;
+}
+
 int panda_selftest_tc_gemm(int M, int N, int K, const float *A, const float *B, float *D, int terms)
 {
     // terms + 10: the same product on CTA pairs (cta_group::2, 256 x 256 tiles);

@@ -195,6 +195,9 @@ cudaError_t launch_reduce_wnorms(const Dev &d, cudaStream_t s);
 cudaError_t launch_reduce_wnorms_set(const Dev *devs, const int2 *blocks, int nblocks, cudaStream_t s);
 cudaError_t launch_fin_tail_set(const Dev *devs, const int2 *blocks, int nblocks, int nnets, cudaStream_t s);
 int set_norm_blocks(int T, int G);
+// FP32 FFMA throughput of the current device in TFLOP/s (best of several
+// timed launches of a loop of independent FMAs on every SM)
+cudaError_t measure_ffma_peak(double *tflops);
 
 // ---- tensor-core path (k_tc.cu) --------------------------------------------
 constexpr int TC_KERNELS = 5;

@@ -10,7 +10,9 @@
 //
 // The array is `g_scratch` below: STATIC_BYTES bytes (about 7.4 MB), sized
 // for networks of at most PANDA_STATIC_MAX_NODES TFs and genes.  Every GPU
-// that loads the library holds it until the process exits.  In host code its
+// that loads the library's device code holds it until the process exits (with
+// CUDA's lazy module loading that happens at the first call on the device, so
+// a caller with a fixed budget makes that call at start-up).  In host code its
 // name only stands for the device array; the device address is looked up once
 // per device with cudaGetSymbolAddress, with that device current, on the
 // first call made on it.  All calls share the array and each call clears it
@@ -189,6 +191,11 @@ extern "C" int panda_step_static(int T, int G, float *dW, float *dP, float *dC, 
     SCU(cudaMemcpyAsync(d.e2tab, e2, sizeof e2, cudaMemcpyHostToDevice, s));
     KernelEvents ke{nullptr, 0};
     SCU(launch_iteration_simt(d, 0, s, ke));
+    SCU(cudaMemcpyAsync(&hc, d.ctl, sizeof hc, cudaMemcpyDeviceToHost, s));
+    SCU(cudaStreamSynchronize(s));
+    // a failed iteration leaves the caller's networks as they were
+    if (hc.status & ST_NONFINITE)
+        return fail(PANDA_ENONFINITE, "panda_step_static: the networks became non-finite (left unchanged)");
 
     // results back into the caller's buffers, diagonals from the FP64 vectors
     SCU(cudaMemcpy2DAsync(dW, (size_t)G * 4, d.W[1], (size_t)d.Gp * 4, (size_t)G * 4, T,
@@ -200,10 +207,7 @@ extern "C" int panda_step_static(int T, int G, float *dW, float *dP, float *dC, 
     k_put_diag<<<ceil_div(T, 256), 256, 0, s>>>(dP, T, T, d.pd);
     k_put_diag<<<ceil_div(G, 256), 256, 0, s>>>(dC, G, G, d.cd);
     SCU(cudaGetLastError());
-    SCU(cudaMemcpyAsync(&hc, d.ctl, sizeof hc, cudaMemcpyDeviceToHost, s));
     SCU(cudaStreamSynchronize(s));
-    if (hc.status & ST_NONFINITE)
-        return fail(PANDA_ENONFINITE, "panda_step_static: the networks became non-finite");
     if (h_out)
         *h_out = hc.h_last;
     return PANDA_OK;

@@ -67,6 +67,7 @@ def _load() -> ctypes.CDLL:
         "panda_step_static": (i, [i, i, vp, vp, vp, f, i, i, pd, vp]),
         "panda_selftest_tc_gemm": (i, [i, i, i, vp, vp, vp, i]),
         "panda_selftest_timeout": (i, []),
+        "panda_measure_ffma_peak": (i, [pd]),
         "panda_create_from_expression": (i, [pvp, i, i, i, vp, vp, vp, popts]),
         "panda_batch_create": (i, [pvp, i, pi, pi, pvp, pvp, pvp, popts]),
         "panda_batch_run": (i, [vp, f, d, i, pi, pd]),
@@ -280,6 +281,13 @@ def panda_selftest_tc_gemm(A, B, terms: int = 3) -> np.ndarray:
     D = np.empty((M, N), np.float32)
     _check(lib.panda_selftest_tc_gemm(M, N, K, _ptr(A), _ptr(B), _ptr(D), int(terms)))
     return D
+
+
+def panda_measure_ffma_peak() -> float:
+    """FP32 FFMA throughput of the current device in TFLOP/s (measured)."""
+    t = ctypes.c_double(0.0)
+    _check(lib.panda_measure_ffma_peak(ctypes.byref(t)))
+    return t.value
 
 
 def panda_selftest_timeout() -> int:

@@ -54,6 +54,10 @@ WORKLOADS = {
     "large1600x30000": Workload("large1600x30000", 1600, 30000, 300, 30, 0.05, 0.01, BASE_SEED + 4),
     # profiling case: same TF count, C (268 MB) still larger than L2, a few GB on the device.
     "prof1000x8192": Workload("prof1000x8192", 1000, 8192, 100, 10, 0.05, 0.01, BASE_SEED + 8),
+    # the human-sized generators at fewer genes: 1000 TFs (ragged in 256-tiles) x 5200 genes,
+    # two waves of phase-1 tiles and a ragged last gene tile; cheap enough for the oracle to
+    # follow a whole converging trajectory.
+    "human1000x5200": Workload("human1000x5200", 1000, 5200, 200, 20, 0.05, 0.01, BASE_SEED + 9),
     # mid-size parity case spanning many tiles with ragged edges.
     "mid250x2100": Workload("mid250x2100", 250, 2100, 100, 10, 0.05, 0.02, BASE_SEED + 7),
 }

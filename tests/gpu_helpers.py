@@ -70,17 +70,43 @@ def oracle_run(orc, W0, P0, C0, alpha=0.1, tol=1e-3, max_iter=200, normalize=Tru
     return dict(W=W, P=P, C=C, iters=n, hist=hist, converged=conv)
 
 
+def _offdiag_max_abs(y: np.ndarray, block: int = 2048) -> float:
+    """max |y_ij| over i != j, in row blocks (full-size C has 2.9e8 entries)."""
+    n, m = y.shape[0], 0.0
+    for r0 in range(0, n, block):
+        b = np.abs(np.asarray(y[r0:r0 + block], np.float64))
+        rr = np.arange(r0, min(n, r0 + block))
+        b[rr - r0, rr] = 0.0
+        m = max(m, float(b.max()))
+    return m
+
+
+def _offdiag_max_err(x: np.ndarray, y: np.ndarray, block: int = 2048) -> float:
+    n, m = x.shape[0], 0.0
+    for r0 in range(0, n, block):
+        d = np.abs(np.asarray(x[r0:r0 + block], np.float64) - y[r0:r0 + block])
+        rr = np.arange(r0, min(n, r0 + block))
+        d[rr - r0, rr] = 0.0
+        m = max(m, float(d.max()))
+    return m
+
+
 def errors(g, o):
     """Max abs error of W, of the off-diagonals of P and C (relative to their
-    scale), and max relative error of the diagonals."""
-    out = {"W": float(np.max(np.abs(g["W"].astype(np.float64) - o["W"])))}
+    scale), and max relative error of the diagonals.  Works through the
+    matrices in row blocks, so full-size networks need no full-size temporaries."""
+    gw, ow = g["W"], o["W"]
+    out = {"W": max(float(np.max(np.abs(np.asarray(gw[r0:r0 + 2048], np.float64) - ow[r0:r0 + 2048])))
+                    for r0 in range(0, gw.shape[0], 2048))}
     for name in ("P", "C"):
-        x, y = g[name].astype(np.float64), o[name]
+        x, y = g[name], o[name]
         n = x.shape[0]
-        off = ~np.eye(n, dtype=bool)
-        scale = max(1.0, float(np.max(np.abs(y[off])))) if n > 1 else 1.0
-        out[name + "off"] = float(np.max(np.abs(x[off] - y[off]))) / scale if n > 1 else 0.0
-        dx, dy = np.diag(x), np.diag(y)
+        if n > 1:
+            scale = max(1.0, _offdiag_max_abs(y))
+            out[name + "off"] = _offdiag_max_err(x, y) / scale
+        else:
+            out[name + "off"] = 0.0
+        dx, dy = np.diag(x).astype(np.float64), np.asarray(np.diag(y), np.float64)
         out[name + "diag"] = float(np.max(np.abs(dx - dy) / np.maximum(np.abs(dy), 1.0)))
     return out
 

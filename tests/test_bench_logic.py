@@ -30,3 +30,44 @@ def test_graph_launch_count():
 def test_set_segments_stay_below_the_earliest_overflow():
     # warm-up at most 20, segment at most 40: 60 < 66, the earliest overflow in the set
     assert 20 + bench.SEG_SET <= 60
+
+
+PEAKS = {"bf16_tflops": 1950.4, "bf16_tflops_sustained": 1744.4, "sm_max_mhz": 2070.0, "hbm_gbs": 6700.2}
+
+
+def test_burst_peak_only_for_a_short_region_at_the_maximum_clock():
+    at_max = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0}
+    p, src = bench.tensor_peak(PEAKS, "measured", at_max, 190.0)
+    assert p == PEAKS["bf16_tflops"] and "burst" in src
+    assert bench.tensor_peak(PEAKS, "measured", {"sm_mhz": 1500.0, "sm_max_mhz": 2070.0}, 190.0)[0] == 1744.4
+    assert bench.tensor_peak(PEAKS, "measured", at_max, 4000.0)[0] == 1744.4
+    assert bench.tensor_peak(PEAKS, "measured", None, 100.0)[0] == 1744.4
+
+
+class _FakePanda:
+    PANDA_FP32, PANDA_BF16X3, PANDA_BF16X2, PANDA_FP8MIX = 0, 1, 2, 3
+
+
+def test_issued_flops_per_precision():
+    T, G = 1000, 17000
+    useful = 2.0 * T * G * G + 2.0 * T * T * G
+    u, issued, units = bench.kernel_flops(_FakePanda, 1, "k_tc_phase1", T, G)
+    assert u == useful and issued == units == 3 * useful
+    assert bench.kernel_flops(_FakePanda, 2, "k_tc_phase1", T, G)[1] == 2 * useful
+    u, issued, units = bench.kernel_flops(_FakePanda, 3, "k_tc_phase1", T, G)
+    assert issued == 2.0 * T * G * G + 3 * 2.0 * T * T * G and units == T * G * G + 6.0 * T * T * G
+    assert bench.kernel_flops(_FakePanda, 1, "k_fin", T, G)[0] == 0.0
+
+
+def test_roofline_reports_both_phase_kernels_and_the_iteration():
+    T, G = 1000, 17000
+    kstats = [("k_tc_phase1", 107.0, 100), ("k_reduce_wnorms", 0.5, 100), ("k_tc_phase2", 76.0, 100),
+              ("k_fin", 2.3, 100), ("k_tail", 0.4, 100)]
+    roof = bench.roofline(_FakePanda, 1, kstats, T, G, "none", PEAKS, "measured",
+                          {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0}, 186.0, None, 530.0)
+    assert roof["kernel"] == "k_tc_phase1" and roof["peak"] == PEAKS["bf16_tflops"]
+    assert abs(roof["frac"] - (2.0 * T * G * G + 2.0 * T * T * G) / 1.07e-3 / 1e12 / 1950.4) < 1e-9
+    names = [k["kernel"] for k in roof["kernels"]]
+    assert names == ["k_tc_phase1", "k_tc_phase2"]
+    it = roof["iteration"]
+    assert abs(it["useful_frac"] * 3 - it["issued_frac"]) < 1e-12
