@@ -47,7 +47,15 @@ extern "C" {
 #define PANDA_ETIMEOUT (-7)    /* a bounded device-side wait expired */
 #define PANDA_EUNSUPPORTED (-8)/* option not available in this build or on this device */
 
-/* Arithmetic of the four products (the epilogues are FP32 in every mode). */
+/* Arithmetic of the four products (the epilogues are FP32 in every mode).
+ * State: W and P are FP32 in every mode, and so is C under PANDA_FP32 and
+ * PANDA_FP8MIX.  Under PANDA_BF16X3 and PANDA_BF16X2 the library holds C only
+ * as the split pair the products read, hi = bf16(x) and lo = bf16(x - hi) of
+ * each FP32 entry x, the same 4 bytes per entry as FP32 (the paper's remark
+ * on memory after Eq. 9: one copy of the largest network, not two).  hi + lo
+ * is within 2^-18 |x| of x, so C entries carry about 17 significant bits
+ * instead of 24; panda_get and panda_get_state return hi + lo (exact in
+ * FP32) with the diagonal from its FP64 vector. */
 typedef enum {
     PANDA_FP32 = 0,   /* FP32 FFMA products (SIMT) */
     PANDA_BF16X3 = 1, /* tensor cores: x = hi + lo in BF16, hi*hi + hi*lo + lo*hi, FP32 accumulation */
@@ -172,8 +180,14 @@ int panda_get_history(panda_ctx *ctx, double *h, int cap, int *n);
 /* Shape, mode and counters of a context. */
 int panda_info(const panda_ctx *ctx, int *T, int *G, int *prec, int *t);
 
-/* Bytes of device memory the context holds. */
+/* Bytes of device memory the context holds between calls. */
 long long panda_device_bytes(const panda_ctx *ctx);
+
+/* The most device memory the context has held at once: under PANDA_BF16X3
+ * and PANDA_BF16X2 a create or panda_set_state also stages C in FP32 (4 G^2
+ * bytes, padded) while it derives the split state, and frees it before it
+ * returns.  PANDA_ALLOC_LIMIT_BYTES caps this peak. */
+long long panda_device_bytes_peak(const panda_ctx *ctx);
 
 /* Measurement support (the paper has no counterpart: it times the whole loop
  * only).  panda_set_profiling(ctx, 1) makes every later iteration record a

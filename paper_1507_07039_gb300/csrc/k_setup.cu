@@ -399,6 +399,19 @@ __global__ void k_standardize_rows(const float *__restrict__ X, int G, int N, __
     }
 }
 
+// out[r][c] = hi[r][c] + lo[r][c] for r <= c < n: the upper triangle of a
+// matrix held as a BF16 split pair (the sum is exact in FP32: lo's last bit is
+// no finer than the last bit of the FP32 value the pair was split from).
+__global__ void k_unsplit_upper(const __nv_bfloat16 *__restrict__ H, const __nv_bfloat16 *__restrict__ L, int n,
+                                int ldi, float *__restrict__ out, int ldo)
+{
+    const int r = blockIdx.y;
+    for (int c = r + blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        const size_t i = (size_t)r * ldi + c;
+        out[(size_t)r * ldo + c] = __bfloat162float(H[i]) + __bfloat162float(L[i]);
+    }
+}
+
 // X_ii = 1 for i < n (a correlation matrix's diagonal)
 __global__ void k_unit_diag(float *X, int n, int ld)
 {
@@ -420,6 +433,16 @@ cudaError_t launch_unit_diag(float *X, int n, int ld, cudaStream_t s)
 {
     k_unit_diag<<<ceil_div(n, 256), 256, 0, s>>>(X, n, ld);
     return cudaGetLastError();
+}
+
+cudaError_t launch_unsplit_sym(const __nv_bfloat16 *H, const __nv_bfloat16 *L, int n, int ldi, float *out, int ldo,
+                              cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    k_unsplit_upper<<<dim3(ceil_div(n, 1024) < 8 ? ceil_div(n, 1024) : 8, n), 256, 0, s>>>(H, L, n, ldi, out, ldo);
+    cudaError_t e = cudaGetLastError();
+    return e ? e : launch_symmetrize(out, n, ldo, s);
 }
 
 cudaError_t launch_symmetrize(float *X, int n, int ld, cudaStream_t s)

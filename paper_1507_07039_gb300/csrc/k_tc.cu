@@ -215,6 +215,22 @@ __device__ __forceinline__ void ld_rows4(const float *p, int ld, float4 (&v)[4])
         v[i] = *reinterpret_cast<const float4 *>(p + (size_t)(8 * i) * ld);
 }
 
+// As ld_rows4 for a matrix held as a BF16 split pair: four values hi + lo from
+// 8-byte loads of each half (the sum is exact in FP32)
+__device__ __forceinline__ void ld_rows4_split(const __nv_bfloat16 *h, const __nv_bfloat16 *l, int ld, float4 (&v)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const size_t o = (size_t)(8 * i) * ld;
+        const uint2 a = *reinterpret_cast<const uint2 *>(h + o), b = *reinterpret_cast<const uint2 *>(l + o);
+        const float2 a0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.x));
+        const float2 a1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.y));
+        const float2 b0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&b.x));
+        const float2 b1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&b.y));
+        v[i] = make_float4(a0.x + b0.x, a0.y + b0.y, a1.x + b1.x, a1.y + b1.y);
+    }
+}
+
 // 16 BF16 values held as 8 packed pairs: two 16-byte stores, or the masked entries
 __device__ __forceinline__ void st16_packed(__nv_bfloat16 *dst, const uint32_t (&p)[8], uint32_t mask)
 {
@@ -1052,7 +1068,9 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
             const float *nrm = isP ? d.rsqW : d.csqW;
             float *X = isP ? d.Poff : d.Coff;
             __nv_bfloat16 *Xh = isP ? d.Ph : d.Ch, *Xl = isP ? d.Pl : d.Cl;
-            const bool wlo = isP || d.split_b;  // C's lo half is a B operand only: none under BF16X2
+            // BF16X3, BF16X2: C is held as its split pair alone (old values hi + lo, no FP32 store)
+            const bool sst = !isP && d.c_split;
+            const bool wlo = isP || d.split_b || sst;
             // split copies of the lower triangle: all of P (phase 1 reads its rows K-major), but of C
             // only inside diagonal 256-blocks (phase 1 reads the rest of C's lower triangle MN-major)
             const bool q8 = d.fp8 && !isP;
@@ -1069,10 +1087,15 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
             // old values, loaded coalesced (8 rows x 64 B per load): lane l takes columns
             // 4 (l & 3) .. + 3 of the warp's rows (l >> 2) + 8 i, i = 0..3 (rows past the network
             // are padding inside the array; their values are never used)
-            const float *xblk = X + (size_t)(k0 + (lane >> 2)) * ld + n0 + 4 * (lane & 3);
+            const size_t xo = (size_t)(k0 + (lane >> 2)) * ld + n0 + 4 * (lane & 3);
+            const float *xblk = sst ? nullptr : X + xo;
             float4 nxt[4];
-            if (n0 + c_begin * 16 < ld)
-                ld_rows4(xblk + c_begin * 16, ld, nxt);
+            if (n0 + c_begin * 16 < ld) {
+                if (sst)
+                    ld_rows4_split(Xh + xo + c_begin * 16, Xl + xo + c_begin * 16, ld, nxt);
+                else
+                    ld_rows4(xblk + c_begin * 16, ld, nxt);
+            }
             epi_bar_p2();
             // on a timed-out wait every epilogue warp still runs the named barriers below
             const bool live = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, d.ctl) &&
@@ -1101,8 +1124,12 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 for (int q = 0; q < 16; ++q)
                     old[q] = inside ? blk[lane * 17 + q] : 0.0f;
                 __syncwarp();  // the block takes the new values next
-                if (c + 1 < c_end && j0 + 16 < ld)
-                    ld_rows4(xblk + (c + 1) * 16, ld, nxt);  // next sub-chunk's old values, in flight meanwhile
+                if (c + 1 < c_end && j0 + 16 < ld) {  // next sub-chunk's old values, in flight meanwhile
+                    if (sst)
+                        ld_rows4_split(Xh + xo + (c + 1) * 16, Xl + xo + (c + 1) * 16, ld, nxt);
+                    else
+                        ld_rows4(xblk + (c + 1) * 16, ld, nxt);
+                }
                 tmem_wait16(accr);
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
@@ -1203,7 +1230,8 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                     split_pair(f[0], f[1], h2[0], l2[0]);
                     split_pair(f[2], f[3], h2[1], l2[1]);
                     if (kk < jj && jj + 3 < nn) {
-                        *reinterpret_cast<float4 *>(X + ro) = make_float4(f[0], f[1], f[2], f[3]);
+                        if (!sst)
+                            *reinterpret_cast<float4 *>(X + ro) = make_float4(f[0], f[1], f[2], f[3]);
                         *reinterpret_cast<uint2 *>(Xh + ro) = make_uint2(h2[0], h2[1]);
                         if (wlo)
                             *reinterpret_cast<uint2 *>(Xl + ro) = make_uint2(l2[0], l2[1]);
@@ -1211,7 +1239,8 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
 #pragma unroll
                         for (int q = 0; q < 4; ++q)
                             if (kk < jj + q && jj + q < nn) {
-                                X[ro + q] = f[q];
+                                if (!sst)
+                                    X[ro + q] = f[q];
                                 reinterpret_cast<uint16_t *>(Xh)[ro + q] = (uint16_t)(h2[q >> 1] >> (16 * (q & 1)));
                                 if (wlo)
                                     reinterpret_cast<uint16_t *>(Xl)[ro + q] =
@@ -1533,10 +1562,8 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales)
             k_to_e4m3<<<1024, 256, 0, s>>>(d.Wt[b], TG, d.Wt8[b], d.f8 + b);
         }
         k_to_e4m3<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.C8, d.f8 + 2);
-    } else if (d.split_b) {
-        k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, d.Cl);
-    } else {
-        k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, nullptr);
+    } else if (d.Coff) {  // C's split pair from the FP32 C being derived (a restored pair is kept)
+        k_split<<<2048, 256, 0, s>>>(d.Coff, (size_t)d.Gp * d.Gp, d.Ch, (d.split_b || d.c_split) ? d.Cl : nullptr);
     }
     if ((e = cudaGetLastError()))
         return e;

@@ -30,8 +30,10 @@ struct panda_ctx {
     Dev d{};
     Ctl *h_ctl = nullptr;  // pinned mirror of the device control block
     std::vector<void *> allocs;
-    long long bytes = 0;
+    long long bytes = 0;       // device memory held between calls
+    long long peak = 0;        // the most held at once (staging buffers included)
     long long limit = -1;
+    float *c_stage = nullptr;  // FP32 C while a create or set_state derives a split-held state
     float e2_alpha = -1.0f;  // alpha for which d.e2tab is filled
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int *d_flags = nullptr;
@@ -105,6 +107,7 @@ int dalloc(panda_ctx *c, T **p, size_t count)
     }
     c->allocs.push_back(q);
     c->bytes += (long long)bytes;
+    c->peak = c->bytes > c->peak ? c->bytes : c->peak;
     e = cudaMemsetAsync(q, 0, bytes, c->stream);
     if (e != cudaSuccess)
         return set_err(c, PANDA_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
@@ -127,12 +130,15 @@ int plan_memory(panda_ctx *c)
     d.diag = c->diag;
     d.split_b = c->prec == PANDA_BF16X2 ? 0 : 1;  // the BF16 products of FP8MIX are BF16X3
     d.fp8 = c->prec == PANDA_FP8MIX ? 1 : 0;
+    // BF16X3 and BF16X2 hold C as its split pair only (FP32 C is staged while the state is derived)
+    d.c_split = (c->prec == PANDA_BF16X3 || c->prec == PANDA_BF16X2) ? 1 : 0;
     for (int b = 0; b < 2; ++b) {
         DALLOC(d.W[b], Tp * Gp);
         DALLOC(d.Wt[b], Gp * Tp);
     }
     DALLOC(d.Poff, Tp * Tp);
-    DALLOC(d.Coff, Gp * Gp);
+    if (!d.c_split)
+        DALLOC(d.Coff, Gp * Gp);
     DALLOC(d.pd, Tp);
     DALLOC(d.cd, Gp);
     DALLOC(d.pdf, Tp);
@@ -179,12 +185,42 @@ int plan_memory(panda_ctx *c)
             DALLOC(d.C8, Gp * Gp);
             DALLOC(d.f8, 4);
             DALLOC(d.f8n, 8);
-        } else {
+        } else {  // C's state: hi and lo (BF16X2 keeps lo too, for the state, not as an operand)
             DALLOC(d.Ch, Gp * Gp);
-            if (d.split_b)
-                DALLOC(d.Cl, Gp * Gp);
+            DALLOC(d.Cl, Gp * Gp);
         }
     }
+    return 0;
+}
+
+// A split-held C (d.c_split) is derived from an FP32 copy: stage_c gives Coff
+// a zeroed Gp x Gp FP32 buffer for that (within PANDA_ALLOC_LIMIT_BYTES,
+// counted in the peak, not in the memory held between calls), unstage_c frees
+// it once the split pair is written.
+int stage_c(panda_ctx *c)
+{
+    Dev &d = c->d;
+    if (!d.c_split || c->c_stage)
+        return 0;
+    const size_t bytes = sizeof(float) * (size_t)c->Gp * c->Gp;
+    if (c->limit >= 0 && c->bytes + (long long)bytes > c->limit)
+        return set_err(c, PANDA_ENOMEM, "device memory plan exceeds PANDA_ALLOC_LIMIT_BYTES");
+    CU(cudaMalloc(&c->c_stage, bytes));
+    const long long held = c->bytes + (long long)bytes;
+    c->peak = held > c->peak ? held : c->peak;
+    CU(cudaMemsetAsync(c->c_stage, 0, bytes, c->stream));
+    d.Coff = c->c_stage;
+    return 0;
+}
+
+int unstage_c(panda_ctx *c)
+{
+    if (!c->c_stage)
+        return 0;
+    CU(cudaStreamSynchronize(c->stream));
+    CU(cudaFree(c->c_stage));
+    c->c_stage = nullptr;
+    c->d.Coff = nullptr;
     return 0;
 }
 
@@ -453,6 +489,9 @@ void free_all(panda_ctx *c)
     if (c->stream)
         cudaStreamSynchronize(c->stream);
     tc_release(c->d);
+    if (c->c_stage)
+        cudaFree(c->c_stage);
+    c->c_stage = nullptr;
     for (void *p : c->allocs)
         cudaFree(p);
     c->allocs.clear();
@@ -535,7 +574,7 @@ int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P
             c->err = std::string("cudaEventCreate: ") + cudaGetErrorString(e);
             return fail(PANDA_ECUDA);
         }
-    if ((rc = plan_memory(c)))
+    if ((rc = plan_memory(c)) || (rc = stage_c(c)))
         return fail(rc);
     if ((rc = upload(c, c->d.W[0], c->Gp, W0, T, G)) || (rc = upload(c, c->d.Poff, c->Tp, P0, T, T)) ||
         (rc = upload(c, c->d.Coff, c->Gp, C0, G, G, ldc)))
@@ -544,7 +583,7 @@ int create_common(panda_ctx **out, int T, int G, const float *W0, const float *P
         return fail(rc);
     if (c->normalize && (rc = zscore_all(c)))
         return fail(rc);
-    if ((rc = derive_state(c, true)) || (rc = push_ctl(c)))
+    if ((rc = derive_state(c, true)) || (rc = push_ctl(c)) || (rc = unstage_c(c)))
         return fail(rc);
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -722,8 +761,42 @@ static int full_matrices(panda_ctx *c)
 {
     if (tensor_prec(c->prec)) {
         CU(launch_symmetrize(c->d.Poff, c->T, c->Tp, c->stream));
-        CU(launch_symmetrize(c->d.Coff, c->G, c->Gp, c->stream));
+        if (!c->d.c_split)
+            CU(launch_symmetrize(c->d.Coff, c->G, c->Gp, c->stream));
     }
+    return 0;
+}
+
+// Whether p is device (or managed) memory of the current device.
+static bool device_pointer(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// C (G x G, dense, host or device) from its split pair: straight into device
+// memory, through a temporary device buffer into host memory.
+static int get_split_c(panda_ctx *c, float *C)
+{
+    Dev &d = c->d;
+    const int G = c->G;
+    if (device_pointer(C)) {
+        CU(launch_unsplit_sym(d.Ch, d.Cl, G, c->Gp, C, G, c->stream));
+        return 0;
+    }
+    float *tmp = nullptr;
+    CU(cudaMalloc(&tmp, sizeof(float) * (size_t)G * G));
+    cudaError_t e = launch_unsplit_sym(d.Ch, d.Cl, G, c->Gp, tmp, G, c->stream);
+    if (!e)
+        e = cudaMemcpyAsync(C, tmp, sizeof(float) * (size_t)G * G, cudaMemcpyDeviceToHost, c->stream);
+    if (!e)
+        e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    CU(e);
     return 0;
 }
 
@@ -744,7 +817,7 @@ static int get_impl(panda_ctx *c, float *W, float *P, float *C)
     for (auto &n : nets) {
         if (!n.dst)
             continue;
-        int rc = download(c, n.dst, n.src, n.ld, n.n, n.n);
+        int rc = (n.dst == C && d.c_split) ? get_split_c(c, C) : download(c, n.dst, n.src, n.ld, n.n, n.n);
         if (rc)
             return rc;
         // diagonal entries, rounded from the FP64 diagonal
@@ -798,10 +871,14 @@ int panda_set_state(panda_ctx *c, const float *W, const float *P, const float *C
     c->cur = 0;
     c->state_ok = false;  // until the new networks are in, validated and their vectors derived
     int rc;
-    if ((rc = upload(c, d.W[0], c->Gp, W, c->T, c->G)) || (rc = upload(c, d.Poff, c->Tp, P, c->T, c->T)) ||
-        (rc = upload(c, d.Coff, c->Gp, C, c->G, c->G)))
+    if ((rc = stage_c(c)))
         return rc;
-    if ((rc = validate(c)) || (rc = derive_state(c, true)))
+    if ((rc = upload(c, d.W[0], c->Gp, W, c->T, c->G)) || (rc = upload(c, d.Poff, c->Tp, P, c->T, c->T)) ||
+        (rc = upload(c, d.Coff, c->Gp, C, c->G, c->G)) || (rc = validate(c)) || (rc = derive_state(c, true))) {
+        unstage_c(c);
+        return rc;
+    }
+    if ((rc = unstage_c(c)))
         return rc;
     c->h_ctl->iters = t;
     c->h_ctl->active = 0;
@@ -830,9 +907,17 @@ std::vector<CkptItem> ckpt_items(panda_ctx *c)
 {
     Dev &d = c->d;
     const size_t Tp = c->Tp, Gp = c->Gp;
-    std::vector<CkptItem> v = {{d.W[c->cur], Tp * Gp * 4}, {d.Poff, Tp * Tp * 4}, {d.Coff, Gp * Gp * 4},
-                               {d.pd, Tp * 8},   {d.cd, Gp * 8},   {d.rsqP, Tp * 4}, {d.csqC, Gp * 4},
-                               {d.rsqW, Tp * 4}, {d.csqW, Gp * 4}, {d.hist, (size_t)HIST_CAP * 8}};
+    std::vector<CkptItem> v = {{d.W[c->cur], Tp * Gp * 4}, {d.Poff, Tp * Tp * 4}};
+    if (d.c_split) {  // C as held: its split pair (the same 4 bytes per entry)
+        v.push_back({d.Ch, Gp * Gp * 2});
+        v.push_back({d.Cl, Gp * Gp * 2});
+    } else {
+        v.push_back({d.Coff, Gp * Gp * 4});
+    }
+    for (CkptItem it : {CkptItem{d.pd, Tp * 8}, CkptItem{d.cd, Gp * 8}, CkptItem{d.rsqP, Tp * 4},
+                        CkptItem{d.csqC, Gp * 4}, CkptItem{d.rsqW, Tp * 4}, CkptItem{d.csqW, Gp * 4},
+                        CkptItem{d.hist, (size_t)HIST_CAP * 8}})
+        v.push_back(it);
     if (d.fp8) {  // the E4M3 scales and latched norm maxima, so that a resumed run continues bit for bit
         v.push_back({d.f8, 4 * sizeof(float)});
         v.push_back({d.f8n, 8 * sizeof(unsigned)});
@@ -940,6 +1025,8 @@ int panda_info(const panda_ctx *c, int *T, int *G, int *prec, int *t)
 }
 
 long long panda_device_bytes(const panda_ctx *c) { return c ? c->bytes : 0; }
+
+long long panda_device_bytes_peak(const panda_ctx *c) { return c ? c->peak : 0; }
 
 int panda_set_profiling(panda_ctx *c, int on)
 {

@@ -9,7 +9,10 @@
 //                          on the tensor-core path made at create and load only
 //                          (column norms, FP8MIX's E4M3 copy)
 //   Poff   Tp x Tp  fp32   P with a zero diagonal (diagonal kept in pd)
-//   Coff   Gp x Gp  fp32   C with a zero diagonal (diagonal kept in cd)
+//   Coff   Gp x Gp  fp32   C with a zero diagonal (diagonal kept in cd); in the
+//                          BF16X3 and BF16X2 modes only while a create or
+//                          set_state derives the state, which is then held as
+//                          the split pair Ch + Cl alone
 //   pd, cd          fp64   diagonals of P and C
 //   rsqP, csqC      fp32   |P_i.|^2 and |C_.j|^2, diagonal included
 //   rsqW, csqW      fp32   |W_i.|^2 and |W_.j|^2 of the current W
@@ -68,6 +71,10 @@ struct Dev {
     // BF16 split copies (tensor-core path only; NULL otherwise)
     __nv_bfloat16 *Wh[2], *Wl[2];  // W^T operands are read from these MN-major
     __nv_bfloat16 *Ph, *Pl, *Ch, *Cl;
+    // 1: C is held only as its split pair Ch + Cl (BF16X3, BF16X2): its upper
+    // triangle and diagonal 256-blocks are the state, Coff is NULL between
+    // calls (a staging buffer while a create or set_state derives the state)
+    int c_split;
     // 1: B operands carry their lo halves too (BF16X3, hi.hi + hi.lo + lo.hi);
     // 0: B operands are BF16 hi only (BF16X2, hi.hi + lo.hi; C's lo half is never made)
     int split_b;
@@ -164,6 +171,11 @@ cudaError_t launch_diag_to_float(const double *d, float *df, int n, cudaStream_t
 cudaError_t launch_scan_nonfinite(const float *X, long long n, int *flag, cudaStream_t s);
 // X[r][c] = X[c][r] for r > c: the full matrix from its upper triangle
 cudaError_t launch_symmetrize(float *X, int n, int ld, cudaStream_t s);
+// out (n x n, row stride ldo) = the symmetric matrix whose upper triangle is
+// held as the BF16 split pair H + L (row stride ldi); diagonal entries are
+// H + L too (callers put the FP64 diagonal in place afterwards)
+cudaError_t launch_unsplit_sym(const __nv_bfloat16 *H, const __nv_bfloat16 *L, int n, int ldi, float *out, int ldo,
+                              cudaStream_t s);
 // Pearson initialisation (Sec. II-A): unit-norm centred rows of X (G x N) as a
 // BF16 split [G][Kp]; flags[0] |= 1 (non-finite) / 2 (zero variance)
 cudaError_t launch_standardize_rows(const float *X, int G, int N, __nv_bfloat16 *Zh, __nv_bfloat16 *Zl, int Kp,

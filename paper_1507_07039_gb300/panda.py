@@ -58,6 +58,7 @@ def _load() -> ctypes.CDLL:
         "panda_get_history": (i, [vp, pd, i, pi]),
         "panda_info": (i, [vp, pi, pi, pi, pi]),
         "panda_device_bytes": (ll, [vp]),
+        "panda_device_bytes_peak": (ll, [vp]),
         "panda_stream": (vp, [vp]),
         "panda_set_profiling": (i, [vp, i]),
         "panda_kernel_count": (i, [vp]),
@@ -251,6 +252,10 @@ def panda_device_bytes(ctx) -> int:
     return int(lib.panda_device_bytes(ctx))
 
 
+def panda_device_bytes_peak(ctx) -> int:
+    return int(lib.panda_device_bytes_peak(ctx))
+
+
 def panda_stream(ctx) -> int:
     return int(lib.panda_stream(ctx) or 0)
 
@@ -363,6 +368,10 @@ class PandaContext:
     @property
     def device_bytes(self):
         return panda_device_bytes(self.h)
+
+    @property
+    def device_bytes_peak(self):
+        return panda_device_bytes_peak(self.h)
 
     @property
     def stream(self):
