@@ -406,8 +406,10 @@ def run_reference(args, wl, rank, world):
 SEG = 100
 # Networks of a set with few TFs and many genes reach that limit first: after
 # 66-70 iterations for T ~ 240-300, G ~ 15000-17000 (measured over set64);
-# a set's warm-up plus one segment stays within 60.
-SEG_SET = 40
+# a set's warm-up (SET_WARM: the 22 schedule trials and one captured chunk)
+# plus one segment stays within 60.
+SET_WARM = 30
+SEG_SET = 30
 
 
 def segments(n: int) -> list[int]:
@@ -662,9 +664,9 @@ def run_set(args, rank, world, local_rank):
     wls = synth.set_of_networks(64)
     nets = [synth.make_inputs(w) for w in wls]
     flops = sum(algorithmic_flops(w.T, w.G) for w in wls)
-    # warm-up: at least the phase-2 schedule trials of the tensor-core set engine (one iteration
-    # each, plus one) and one captured chunk, so that neither falls in the timed region
-    warm = min(max(args.warmup, 16) if prec != panda.PANDA_FP32 else args.warmup, 20)
+    # warm-up: the schedule trials of the tensor-core set engine (one warm-up iteration, then three
+    # per candidate: 22) and one captured chunk of 8, so that neither falls in the timed region
+    warm = SET_WARM if prec != panda.PANDA_FP32 else min(args.warmup, SET_WARM)
     # the diagonals' e^{2 alpha t} growth (see SEG): more than SEG_SET timed iterations run as
     # segments, each on a freshly created set with its own warm-up, the creation untimed
     seg_set = min(SEG_SET, 60 - warm)
@@ -707,8 +709,10 @@ def run_set(args, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "useful_tflops": flops * args.steps / sec / 1e12, "clocks": ck,
             "schedule": None if sched is None else {
-                "epilogue_weight": sched[0], "trial_phase2_ms": [round(t, 3) for t in sched[1]],
-                "candidates": [48, 96, 192, 384, 768]}}), flush=True)
+                "phase1": sched["p1_names"][sched["p1"]], "phase2": sched["p2_names"][sched["p2"]],
+                "phase1_trial_ms": dict(zip(sched["p1_names"], [round(t, 3) for t in sched["p1_ms"]])),
+                "phase2_trial_ms": dict(zip(sched["p2_names"], [round(t, 3) for t in sched["p2_ms"]])),
+                "trials": "median of 3 iterations per candidate"}}), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

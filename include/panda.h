@@ -252,9 +252,8 @@ void panda_destroy(panda_ctx *ctx);
  * launch per phase over every network's tiles (phase 1 over all their W'
  * tiles, phase 2 persistent over one longest-first schedule of all their P and
  * C tiles, then the norm and stop kernels over all their rows), a chunk of
- * iterations captured as one CUDA graph.  The phase-2 schedule is autotuned:
- * the first iterations a batch runs try schedules built for several epilogue
- * weights, one iteration each, and the fastest is kept.  A tile's result does
+ * iterations captured as one CUDA graph.  The schedules of both phases are
+ * autotuned on the first iterations a batch runs (panda_batch_schedule).  A tile's result does
  * not depend on the schedule, so every network's results equal, bit for bit,
  * those of the same network run alone.
  * FP32: every network queues its chunks (a CUDA graph each) on its own stream. */
@@ -280,13 +279,25 @@ int panda_batch_get(panda_batch *b, int k, float *W, float *P, float *C);
 int panda_batch_size(const panda_batch *b);
 panda_ctx *panda_batch_context(panda_batch *b, int k);
 
-/* The phase-2 schedule autotuning of a tensor-core batch (no paper
- * counterpart): *epi receives the epilogue weight of the schedule in use (MMA
- * issue slots per tile), trial_ms[q] (n_trials entries, may be NULL) the
- * phase-2 time of trial q in ms (0 while not yet run), *done whether the
- * trials are over.  Returns the number of trial schedules, 0 for an FP32
- * batch, PANDA_EINVAL for NULL b. */
-int panda_batch_schedule(const panda_batch *b, int *epi, float *trial_ms, int n_trials, int *done);
+/* The schedule autotuning of a tensor-core batch (no paper counterpart).
+ * Both phases run on persistent CTA pairs over longest-first (LPT) lists of
+ * every network's tiles; the candidates differ in the order of a network's
+ * phase-1 tiles (which operand rows neighbouring tiles share in L2) and in
+ * the phase-2 cost model (MMA slots, or the larger of MMA and HBM time),
+ * epilogue weight and list order (panda_batch_schedule_name describes each).
+ * The first iterations a batch runs are the trials: one warm-up, then three
+ * iterations per phase-1 candidate (timing phase 1), the fastest by median
+ * kept, then three per phase-2 candidate (timing phase 2).  *p1, *p2 receive
+ * the candidates in use; p1_ms[q] (n1 entries) and p2_ms[q] (n2 entries),
+ * each may be NULL, the median trial times in ms (0 while not yet run);
+ * *done whether the trials are over.  Returns 1 for a tensor-core batch, 0 for
+ * an FP32 batch (no schedules), PANDA_EINVAL for NULL b. */
+int panda_batch_schedule(const panda_batch *b, int *p1, int *p2, float *p1_ms, int n1, float *p2_ms, int n2,
+                         int *done);
+
+/* Description of schedule candidate k of phase 1 (phase = 1) or phase 2
+ * (phase = 2); NULL past the last candidate. */
+const char *panda_batch_schedule_name(int phase, int k);
 
 const char *panda_batch_last_error(const panda_batch *b);
 void panda_batch_destroy(panda_batch *b);

@@ -623,7 +623,7 @@ cudaError_t launch_iteration_simt(const Dev &d, int cur, cudaStream_t s, KernelE
 namespace panda {
 namespace {
 
-constexpr int FFMA_CHAINS = 8, FFMA_LOOP = 2048, FFMA_THREADS = 512;
+constexpr int FFMA_CHAINS = 8, FFMA_LOOP = 4096, FFMA_THREADS = 512;
 
 // Every thread runs FFMA_CHAINS independent chains x <- x * a + b for
 // FFMA_LOOP rounds (a, b are launch arguments, so nothing is folded); the
@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(FFMA_THREADS) k_ffma_loop(float a, float b, fl
 #pragma unroll
     for (int c = 0; c < FFMA_CHAINS; ++c)
         x[c] = (float)(threadIdx.x + c) * 1e-3f;
-#pragma unroll 4
+#pragma unroll 32  // 256 FMAs per trip through the loop: its counter and branch are noise
     for (int it = 0; it < FFMA_LOOP; ++it)
 #pragma unroll
         for (int c = 0; c < FFMA_CHAINS; ++c)

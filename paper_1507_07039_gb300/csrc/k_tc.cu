@@ -66,7 +66,8 @@ struct SetArgs {
     const Dev *devs;       // the networks' device state
     const TcMaps *maps;    // their tensor maps (64-byte aligned, in global memory)
     const int *parity;     // W buffer of a network = (parity + its iteration count) & 1
-    const int4 *items1;    // phase 1: one (network, mt, nt, 0) per CTA pair
+    const int4 *items1;    // phase 1: (network, mt, nt, cost) tiles, listed per CTA pair
+    const int *p1_off;     // phase 1: per CTA pair, its range of items1
     const int *sched_off;  // phase 2: per CTA pair, its range of sched
     const int *sched;      // phase 2: packed tiles (as for one network)
     const int *sched_net;  // phase 2: the network of each tile
@@ -520,17 +521,61 @@ constexpr size_t phase1_smem()
            (P1_COLVEC + P1_COLRED + P1_ROWRED + EPI1 * P1_BLK) * sizeof(float) + EPI1 * sizeof(double);
 }
 
+__device__ __forceinline__ Sync1 &phase1_sync()
+{
+    extern __shared__ uint8_t smem_raw[];
+    return *reinterpret_cast<Sync1 *>(align1024(smem_raw) + ST1 * STAGE1);
+}
+
+// Set-up of a phase-1 CTA, once per kernel: the pipeline barriers (their
+// phases then run on over every tile the CTA computes, counted by the stage
+// counter g and the tile counter of phase1_tile) and the pair's 512 TMEM
+// columns (a CTA gives up its allocation permit after the first allocation,
+// so a persistent CTA keeps them over all its tiles).  Released by
+// phase1_tmem_free.
+__device__ __forceinline__ void phase1_tmem_alloc()
+{
+    Sync1 &sy = phase1_sync();
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < ST1; ++q) {
+            mbar_init(&sy.full[q], 1);
+            mbar_init(&sy.empty[q], 1);
+        }
+        mbar_init(&sy.accum, 1);
+        sy.abort = 0;
+        fence_mbar_init();
+    }
+    if ((threadIdx.x >> 5) == 1)
+        tmem_alloc_pair(&sy.tmem, 512);
+    tc_fence_before();
+    cluster_sync();  // both CTAs' barriers and TMEM address are ready before any cross-CTA signal
+    tc_fence_after();
+}
+__device__ __forceinline__ void phase1_tmem_free()
+{
+    tc_fence_before();
+    cluster_sync();  // both CTAs release together (also when a pair had no tile to run)
+    if ((threadIdx.x >> 5) == 1) {
+        tc_fence_after();
+        tmem_dealloc_pair(phase1_sync().tmem, 512);
+    }
+}
+
 // The body of phase 1 for the tile (mt, nt) of one network: maps and d are
 // that network's (kernel parameters for one network, entries of arrays in
-// global memory for a set), cur its current W buffer.
-__device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, int cur, int mt, int nt)
+// global memory for a set), cur its current W buffer.  g counts the pipeline
+// stages and tile the tiles this CTA has run before (barrier phases follow
+// them); both advance here.  Both CTAs of the pair run every call together and
+// end it at a cluster barrier, after which TMEM is free for the next tile.
+__device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, int cur, int mt, int nt, int &g,
+                                            int &tile)
 {
     Ctl *ctl = d.ctl;
     if (!ctl->active)  // both CTAs of a pair see the same value and leave together
         return;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *stages = align1024(smem_raw);
-    Sync1 &sy = *reinterpret_cast<Sync1 *>(stages + ST1 * STAGE1);
+    Sync1 &sy = phase1_sync();
     float *colvec = reinterpret_cast<float *>(stages + ST1 * STAGE1 + ((sizeof(Sync1) + 15) & ~size_t(15)));
     float *colred = colvec + P1_COLVEC;
     float *rowred = colred + P1_COLRED;
@@ -544,30 +589,23 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
     // k-blocks: R-num over TFs (64 BF16 per row), then A-num over genes (64 BF16, or 128 E4M3 under FP8MIX)
     const int nR = d.Tp / BK, nk = nR + d.Gp / (d.fp8 ? 2 * BK : BK);
 
+    const int g0 = g;      // stages run by this CTA before this tile
+    const uint32_t tpar = (uint32_t)tile & 1u;  // phase of the accumulator barrier for this tile
+    g += nk;
+    ++tile;
     if (threadIdx.x == 0) {
-        for (int q = 0; q < ST1; ++q) {
-            mbar_init(&sy.full[q], 1);
-            mbar_init(&sy.empty[q], 1);
-        }
-        mbar_init(&sy.accum, 1);
-        sy.abort = 0;
         sy.issued = 0;
         sy.consumed = 0;
-        fence_mbar_init();
     }
-    if (warp == 1)
-        tmem_alloc_pair(&sy.tmem, 512);
-    tc_fence_before();
-    cluster_sync();
-    tc_fence_after();
+    __syncthreads();
 
     if (warp == 0) {
         if (lane == 0) {  // ---- TMA producer (both CTAs; completion counted on the even CTA) ----
             const int nb0 = n0 + 128 * (int)rank;  // this CTA's half of the B rows
             int kb = 0;
             for (; kb < nk; ++kb) {
-                const int st = kb % ST1;
-                if (!wait_bounded(&sy.empty[st], ((uint32_t)(kb / ST1) & 1u) ^ 1u, &sy.abort, ctl))
+                const int st = (g0 + kb) % ST1;
+                if (!wait_bounded(&sy.empty[st], ((uint32_t)((g0 + kb) / ST1) & 1u) ^ 1u, &sy.abort, ctl))
                     break;
                 const uint32_t fb = mapa_shared(smem_u32(&sy.full[st]), 0);
                 if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half, 2 of E4M3
@@ -612,8 +650,8 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
             constexpr uint32_t idesc = idesc_bf16_f32(256, 256);
             int kb = 0;
             for (; kb < nk; ++kb) {
-                const int st = kb % ST1;
-                if (!wait_bounded(&sy.full[st], (uint32_t)(kb / ST1) & 1u, &sy.abort, ctl))
+                const int st = (g0 + kb) % ST1;
+                if (!wait_bounded(&sy.full[st], (uint32_t)((g0 + kb) / ST1) & 1u, &sy.abort, ctl))
                     break;
                 tc_fence_after();
                 const uint32_t base = smem_u32(stages + (size_t)st * STAGE1);
@@ -676,7 +714,7 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
         float nxt[16];
         ld16(wrow, nxt);
         epi_bar2();
-        const bool live = wait_bounded(&sy.accum, 0, &sy.abort, ctl) && !*(volatile int *)&sy.abort;
+        const bool live = wait_bounded(&sy.accum, tpar, &sy.abort, ctl) && !*(volatile int *)&sy.abort;
         tc_fence_after();
         const float a = ctl->alpha, keep = 1.0f - a, halfa = 0.5f * a;
         float rowsq = 0.0f, hsum = 0.0f;
@@ -778,12 +816,8 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
     __syncthreads();
     if (threadIdx.x == 0 && rank == 0)  // loads counted here but not consumed (abort only)
         for (int kb = sy.consumed; kb < sy.consumed + ST1 && kb < sy.issued; ++kb)
-            wait_bounded(&sy.full[kb % ST1], (uint32_t)(kb / ST1) & 1u, &sy.abort, ctl, true);
-    cluster_sync();
-    if (warp == 1) {
-        tc_fence_after();
-        tmem_dealloc_pair(sy.tmem, 512);
-    }
+            wait_bounded(&sy.full[(g0 + kb) % ST1], (uint32_t)((g0 + kb) / ST1) & 1u, &sy.abort, ctl, true);
+    cluster_sync();  // neither CTA goes on while the pair may still signal it
 }
 
 
@@ -791,15 +825,27 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
     k_tc_phase1(const __grid_constant__ TcMaps maps, const __grid_constant__ Dev d, int cur)
 {
-    phase1_tile(maps, d, cur, blockIdx.x >> 1, blockIdx.y);
+    if (!d.ctl->active)  // both CTAs of a pair see the same value and leave together
+        return;
+    phase1_tmem_alloc();
+    int g = 0, tile = 0;
+    phase1_tile(maps, d, cur, blockIdx.x >> 1, blockIdx.y, g, tile);
+    phase1_tmem_free();
 }
 
-// A set of networks: one pair per entry of the work list, each entry a tile of one network.
+// A set of networks: persistent CTA pairs, each over its host-built list of
+// (network, mt, nt) tiles; tiles of networks that have stopped are skipped by
+// both CTAs alike.
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1) k_tc_phase1_set(const SetArgs a)
 {
-    const int4 w = a.items1[blockIdx.x >> 1];  // (network, mt, nt, -)
-    const Dev &d = a.devs[w.x];
-    phase1_tile(a.maps[w.x], d, set_cur(a, w.x), w.y, w.z);
+    const int pair = blockIdx.x >> 1;
+    phase1_tmem_alloc();
+    int g = 0, tile = 0;
+    for (int q = a.p1_off[pair]; q < a.p1_off[pair + 1]; ++q) {
+        const int4 w = a.items1[q];  // (network, mt, nt, cost)
+        phase1_tile(a.maps[w.x], a.devs[w.x], set_cur(a, w.x), w.y, w.z, g, tile);
+    }
+    phase1_tmem_free();
 }
 
 // ---------------------------------------------------------------------------
@@ -1446,59 +1492,95 @@ int tile_cost(const Dev &d, bool isP, int epi)
     return (d.Tp / BK) * 4 * terms + epi;
 }
 
-// Longest-processing-time assignment of the upper-triangle 256 x 256 tiles of
-// P and C of every network to `pairs` persistent CTA pairs.  Outputs: per pair
-// a range off[p] .. off[p + 1] of tiles (packed: bit 31 = P, bits 16-30 = row
-// block, bits 0-15 = column block) and nets (the network of each tile).  The
-// order of tiles within a pair's list is the order they were assigned
-// (longest first); their results do not depend on the assignment.
-void build_schedule_set(const std::vector<const Dev *> &ds, int pairs, int epi, std::vector<int> &off,
-                        std::vector<int> &tiles, std::vector<int> &nets)
+// Longest-processing-time assignment of weighted items to `pairs` lists
+// (the heaviest item to the least loaded list); interleave: each list is then
+// reordered heaviest, lightest, second heaviest, ... so that tensor-bound and
+// memory-bound work alternate in time on every pair.
+template <class Item>
+void lpt_lists(std::vector<std::pair<long long, Item>> all, int pairs, bool interleave, std::vector<int> &off,
+               std::vector<Item> &out)
 {
-    struct T_ { int cost, code, net; };
-    std::vector<T_> all;
-    for (int k = 0; k < (int)ds.size(); ++k) {
-        const Dev &d = *ds[k];
-        const int nbP = ceil_div(d.Tp, N2), nbC = ceil_div(d.Gp, N2);
-        const int cP = tile_cost(d, true, epi), cC = tile_cost(d, false, epi);
-        for (int bm = 0; bm < nbP; ++bm)
-            for (int bn = bm; bn < nbP; ++bn)
-                all.push_back({cP, (int)(0x80000000u | ((uint32_t)bm << 16) | (uint32_t)bn), k});
-        for (int bm = 0; bm < nbC; ++bm)
-            for (int bn = bm; bn < nbC; ++bn)
-                all.push_back({cC, (bm << 16) | bn, k});
-    }
-    std::stable_sort(all.begin(), all.end(), [](const T_ &a, const T_ &b) { return a.cost > b.cost; });
-    if (pairs > (int)all.size())
-        pairs = (int)all.size();
-    std::vector<std::vector<std::pair<int, int>>> lists(pairs);
+    std::stable_sort(all.begin(), all.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    std::vector<std::vector<Item>> lists(std::max(pairs, 1));
     using L = std::pair<long long, int>;
     std::priority_queue<L, std::vector<L>, std::greater<L>> heap;
-    for (int c = 0; c < pairs; ++c)
+    for (int c = 0; c < (int)lists.size(); ++c)
         heap.push({0, c});
     for (const auto &t : all) {
         L top = heap.top();
         heap.pop();
-        lists[top.second].push_back({t.code, t.net});
-        heap.push({top.first + t.cost, top.second});
+        lists[top.second].push_back(t.second);
+        heap.push({top.first + t.first, top.second});
     }
     off.assign(1, 0);
-    tiles.clear();
-    nets.clear();
-    for (const auto &l : lists) {
-        for (const auto &t : l) {
-            tiles.push_back(t.first);
-            nets.push_back(t.second);
+    out.clear();
+    for (auto &l : lists) {
+        if (interleave) {
+            std::vector<Item> m;
+            for (size_t i = 0, j = l.size(); i < j; ++i) {
+                m.push_back(l[i]);
+                if (i + 1 < j)
+                    m.push_back(l[--j]);
+            }
+            l.swap(m);
         }
-        off.push_back((int)tiles.size());
+        out.insert(out.end(), l.begin(), l.end());
+        off.push_back((int)out.size());
     }
 }
 
-// One network, epilogue weight of 16 BF16X3 k-blocks (192 MMA slots).
+// Bytes one phase-2 tile moves through HBM in its epilogue (old values read,
+// new values and split copies written; operands come from L2), per entry.
+int tile_epilogue_bytes(const Dev &d, bool isP)
+{
+    if (isP)
+        return 16;  // FP32 old + FP32 new + split copy of both triangles
+    if (d.fp8)
+        return 10;  // FP32 old + new, E4M3 row and mirrored copies
+    return d.c_split ? 8 : 12;  // split pair old + new (or FP32 old + new + split copy)
+}
+
+constexpr long long BYTES_PER_SLOT = 7200;  // HBM bytes per pair in one BF16 MMA slot (82 ns at the dense peak)
+
+// Phase-2 candidates: cost model, epilogue weight, order
+struct P2Spec {
+    int roofline, epi, interleave;
+};
+const P2Spec TC_P2_SPEC[TC_P2_CANDS] = {{0, 192, 0}, {1, 48, 0}, {1, 192, 0}, {1, 192, 1}, {1, 768, 0}};
+
+// One phase-2 schedule of every network's upper-triangle P and C tiles.
+void build_p2(const std::vector<const Dev *> &ds, int pairs, const P2Spec &sp, std::vector<int> &off,
+              std::vector<int> &tiles, std::vector<int> &nets)
+{
+    std::vector<std::pair<long long, std::pair<int, int>>> all;
+    for (int k = 0; k < (int)ds.size(); ++k) {
+        const Dev &d = *ds[k];
+        for (int isP = 1; isP >= 0; --isP) {
+            const int nb = ceil_div(isP ? d.Tp : d.Gp, N2);
+            long long c = tile_cost(d, isP != 0, 0);
+            if (sp.roofline)
+                c = std::max(c, (long long)tile_epilogue_bytes(d, isP != 0) * N2 * N2 / BYTES_PER_SLOT);
+            c += sp.epi;
+            for (int bm = 0; bm < nb; ++bm)
+                for (int bn = bm; bn < nb; ++bn)
+                    all.push_back({c, {(int)((isP ? 0x80000000u : 0u) | ((uint32_t)bm << 16) | (uint32_t)bn), k}});
+        }
+    }
+    std::vector<std::pair<int, int>> out;
+    lpt_lists(all, std::min<int>(pairs, (int)all.size()), sp.interleave != 0, off, out);
+    tiles.clear();
+    nets.clear();
+    for (auto &t : out) {
+        tiles.push_back(t.first);
+        nets.push_back(t.second);
+    }
+}
+
+// One network: the first candidate (LPT on MMA slots, epilogue weight 192).
 void build_schedule(const Dev &d, int pairs, std::vector<int> &off, std::vector<int> &tiles)
 {
     std::vector<int> nets;
-    build_schedule_set({&d}, pairs, 192, off, tiles, nets);
+    build_p2({&d}, pairs, TC_P2_SPEC[0], off, tiles, nets);
 }
 
 cudaError_t set_smem_limits()
@@ -1532,6 +1614,14 @@ cudaError_t set_smem_limits()
 }
 
 }  // namespace
+
+// Phase-1 candidates: the order of a network's tiles (LPT over persistent pairs by main-loop length)
+const char *const TC_P1_NAMES[TC_P1_CANDS] = {"tiles of a gene block together (C rows shared in L2)",
+                                              "tiles of a TF block together (W rows shared in L2)"};
+// Phase-2 candidates (cost model, epilogue weight, order), as in TC_P2_SPEC
+const char *const TC_P2_NAMES[TC_P2_CANDS] = {
+    "LPT on MMA slots + 192", "LPT on max(MMA, HBM) + 48", "LPT on max(MMA, HBM) + 192",
+    "LPT on max(MMA, HBM) + 192, heavy and light tiles alternating", "LPT on max(MMA, HBM) + 768"};
 
 bool tc_supported()
 {
@@ -1642,20 +1732,23 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
 
 // ---- sets of networks: one launch per phase over all networks' tiles ---------------
 struct TcSet {
-    int n = 0, diag = 0;
+    int n = 0, diag = 0, pairs = 0;
     Dev *devs = nullptr;      // device copies of the networks' Dev
     TcMaps *maps = nullptr;   // their tensor maps
     int *parity = nullptr;
-    int4 *items1 = nullptr;
-    int nitems1 = 0;
     int2 *blocks = nullptr;
     int nblocks = 0;
     Ctl *gather = nullptr;
-    struct Cand {
-        int epi = 0, pairs = 0;
+    struct P1 {               // a phase-1 schedule: per pair, a list of (network, mt, nt, cost)
+        int4 *items = nullptr;
+        int *off = nullptr;
+    };
+    struct P2 {               // a phase-2 schedule: per pair, a list of packed tiles and their networks
+        int pairs = 0;
         int *off = nullptr, *tiles = nullptr, *nets = nullptr;
     };
-    std::vector<Cand> cands;  // phase-2 schedules, one per epilogue weight
+    std::vector<P1> p1;
+    std::vector<P2> p2;
 };
 
 namespace {
@@ -1667,9 +1760,8 @@ cudaError_t upload(T **dst, const std::vector<T> &v)
         e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;
 }
-}  // namespace
 
-const int TC_SET_EPI[TC_SET_CANDS] = {48, 96, 192, 384, 768};
+}  // namespace
 
 cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out)
 {
@@ -1682,36 +1774,47 @@ cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out)
     t->diag = ds[0]->diag;
     std::vector<Dev> hd;
     std::vector<TcMaps> hm;
-    std::vector<int4> it;
     std::vector<int2> bl;
     for (int k = 0; k < t->n; ++k) {
         const Dev &d = *ds[k];
         hd.push_back(d);
         hm.push_back(static_cast<const TcHost *>(d.tc_host)->maps);
-        for (int mt = 0; mt < d.Tp / 256; ++mt)
-            for (int nt = 0; nt < d.Gp / 256; ++nt)
-                it.push_back(make_int4(k, mt, nt, d.Tp / BK + d.Gp / (d.fp8 ? 2 * BK : BK)));
         for (int b = 0; b < set_norm_blocks(d.T, d.G); ++b)
             bl.push_back(make_int2(k, b));
     }
-    // the block scheduler starts pairs in index order: longest main loops first
-    std::stable_sort(it.begin(), it.end(), [](const int4 &a, const int4 &b) { return a.w > b.w; });
-    t->nitems1 = (int)it.size();
     t->nblocks = (int)bl.size();
     int dev = 0, nsm = 0;
     if (!(e = cudaGetDevice(&dev)) && !(e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) &&
-        !(e = upload(&t->devs, hd)) && !(e = upload(&t->maps, hm)) && !(e = upload(&t->items1, it)) &&
-        !(e = upload(&t->blocks, bl)) && !(e = cudaMalloc(&t->parity, t->n * sizeof(int))) &&
-        !(e = cudaMemset(t->parity, 0, t->n * sizeof(int))) && !(e = cudaMalloc(&t->gather, t->n * sizeof(Ctl)))) {
-        for (int q = 0; q < TC_SET_CANDS && !e; ++q) {
+        !(e = upload(&t->devs, hd)) && !(e = upload(&t->maps, hm)) && !(e = upload(&t->blocks, bl)) &&
+        !(e = cudaMalloc(&t->parity, t->n * sizeof(int))) && !(e = cudaMemset(t->parity, 0, t->n * sizeof(int))) &&
+        !(e = cudaMalloc(&t->gather, t->n * sizeof(Ctl)))) {
+        t->pairs = nsm / 2;
+        for (int q = 0; q < TC_P1_CANDS && !e; ++q) {  // phase 1: persistent pairs over LPT lists
+            std::vector<std::pair<long long, int4>> all;
+            for (int k = 0; k < t->n; ++k) {
+                const Dev &d = *ds[k];
+                const int nk = d.Tp / BK + d.Gp / (d.fp8 ? 2 * BK : BK), nmt = d.Tp / 256, nnt = d.Gp / 256;
+                for (int a = 0; a < (q == 0 ? nnt : nmt); ++a)
+                    for (int b = 0; b < (q == 0 ? nmt : nnt); ++b)
+                        all.push_back({nk, q == 0 ? make_int4(k, b, a, nk) : make_int4(k, a, b, nk)});
+            }
+            std::vector<int> off;
+            std::vector<int4> items;
+            lpt_lists(all, std::min<int>(t->pairs, (int)all.size()), false, off, items);
+            off.resize(t->pairs + 1, off.back());  // pairs beyond the items get empty lists
+            TcSet::P1 c;
+            if (!(e = upload(&c.items, items)))
+                e = upload(&c.off, off);
+            t->p1.push_back(c);
+        }
+        for (int q = 0; q < TC_P2_CANDS && !e; ++q) {
             std::vector<int> off, tiles, nets;
-            build_schedule_set(ds, nsm / 2, TC_SET_EPI[q], off, tiles, nets);
-            TcSet::Cand c;
-            c.epi = TC_SET_EPI[q];
+            build_p2(ds, t->pairs, TC_P2_SPEC[q], off, tiles, nets);
+            TcSet::P2 c;
             c.pairs = (int)off.size() - 1;
             if (!(e = upload(&c.off, off)) && !(e = upload(&c.tiles, tiles)))
                 e = upload(&c.nets, nets);
-            t->cands.push_back(c);
+            t->p2.push_back(c);
         }
     }
     if (e) {
@@ -1727,22 +1830,26 @@ cudaError_t tc_set_parity(TcSet *t, const std::vector<int> &parity, cudaStream_t
     return cudaMemcpyAsync(t->parity, parity.data(), t->n * sizeof(int), cudaMemcpyHostToDevice, s);
 }
 
-cudaError_t tc_set_launch(TcSet *t, int cand, cudaStream_t s, cudaEvent_t p2_begin, cudaEvent_t p2_end)
+cudaError_t tc_set_launch(TcSet *t, int p1, int p2, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                          cudaEvent_t ev2)
 {
-    const TcSet::Cand &c = t->cands[cand];
-    SetArgs a{t->devs, t->maps, t->parity, t->items1, c.off, c.tiles, c.nets};
-    k_tc_phase1_set<<<2 * t->nitems1, THREADS1, phase1_smem(), s>>>(a);
+    const TcSet::P1 &a1 = t->p1[p1];
+    const TcSet::P2 &c = t->p2[p2];
+    SetArgs a{t->devs, t->maps, t->parity, a1.items, a1.off, c.off, c.tiles, c.nets};
+    if (ev0)
+        cudaEventRecord(ev0, s);
+    k_tc_phase1_set<<<2 * t->pairs, THREADS1, phase1_smem(), s>>>(a);
     cudaError_t e = launch_reduce_wnorms_set(t->devs, t->blocks, t->nblocks, s);
     if (e)
         return e;
-    if (p2_begin)
-        cudaEventRecord(p2_begin, s);
+    if (ev1)
+        cudaEventRecord(ev1, s);
     if (t->diag == 2)
         k_tc_phase2_set<true><<<2 * c.pairs, THREADS2, phase2_smem<true>(), s>>>(a);
     else
         k_tc_phase2_set<false><<<2 * c.pairs, THREADS2, phase2_smem<false>(), s>>>(a);
-    if (p2_end)
-        cudaEventRecord(p2_end, s);
+    if (ev2)
+        cudaEventRecord(ev2, s);
     return launch_fin_tail_set(t->devs, t->blocks, t->nblocks, t->n, s);
 }
 
@@ -1760,10 +1867,13 @@ void tc_set_destroy(TcSet *t)
     cudaFree(t->devs);
     cudaFree(t->maps);
     cudaFree(t->parity);
-    cudaFree(t->items1);
     cudaFree(t->blocks);
     cudaFree(t->gather);
-    for (auto &c : t->cands) {
+    for (auto &c : t->p1) {
+        cudaFree(c.items);
+        cudaFree(c.off);
+    }
+    for (auto &c : t->p2) {
         cudaFree(c.off);
         cudaFree(c.tiles);
         cudaFree(c.nets);

@@ -7,6 +7,7 @@
 
 #include <nvtx3/nvToolsExt.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -1134,10 +1135,15 @@ struct panda_batch {
     cudaGraphExec_t gexec = nullptr;
     int graph_iters = 8;
     Ctl *h_ctls = nullptr;               // pinned: every network's control block after a chunk
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    int tune_next = 0;                   // phase-2 schedule autotuning: next trial (warm-up first)
-    int chosen = 2;                      // the schedule in use (an index into TC_SET_EPI)
-    float tune_ms[TC_SET_CANDS] = {};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    // schedule autotuning: one warm-up iteration, then TUNE_REPS iterations per phase-1
+    // candidate (phase-1 time), then per phase-2 candidate (phase-2 time); medians decide
+    static constexpr int TUNE_REPS = 3;
+    int tune_step = 0;                   // trial iterations run so far
+    int p1 = 0, p2 = 0;                  // the schedules in use
+    float p1_ms[TC_P1_CANDS][TUNE_REPS] = {}, p2_ms[TC_P2_CANDS][TUNE_REPS] = {};
+    float p1_med[TC_P1_CANDS] = {}, p2_med[TC_P2_CANDS] = {};
+    static constexpr int TUNE_STEPS = 1 + (TC_P1_CANDS + TC_P2_CANDS) * TUNE_REPS;
 };
 
 namespace {
@@ -1167,7 +1173,7 @@ int batch_graph(panda_batch *b)
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
     for (int k = 0; k < b->graph_iters && !e; ++k)
-        e = tc_set_launch(b->set, b->chosen, b->stream, nullptr, nullptr);
+        e = tc_set_launch(b->set, b->p1, b->p2, b->stream, nullptr, nullptr, nullptr);
     cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
     if (!e)
         e = e2;
@@ -1183,19 +1189,35 @@ int batch_graph(panda_batch *b)
     return 0;
 }
 
+float median3(const float (&v)[panda_batch::TUNE_REPS])
+{
+    float a[panda_batch::TUNE_REPS];
+    std::copy(v, v + panda_batch::TUNE_REPS, a);
+    std::sort(a, a + panda_batch::TUNE_REPS);
+    return a[panda_batch::TUNE_REPS / 2];
+}
+
 // One chunk of the set engine: while the schedule autotuning is unfinished, a
-// single iteration with the next trial schedule, its phase 2 timed (trial 0
-// warms up with the default schedule; trials 1.. time each candidate, then the
-// fastest is kept); afterwards the captured graph.  Every schedule gives the
-// same results.  Then all control blocks are read back.
+// single iteration with the next trial's schedules, its phases timed by CUDA
+// events (the warm-up first, then TUNE_REPS iterations of each phase-1
+// candidate with the default phase 2, the fastest by median kept, then of each
+// phase-2 candidate); afterwards the captured graph with the chosen pair.
+// Every schedule gives the same results.  Then all control blocks are read back.
 int batch_chunk(panda_batch *b)
 {
     cudaError_t e;
-    const bool tuning = b->tune_next <= TC_SET_CANDS;
+    constexpr int R = panda_batch::TUNE_REPS;
+    const int step = b->tune_step;
+    const bool tuning = step < panda_batch::TUNE_STEPS;
+    int which = -1, cand = -1;  // phase being tried (1 or 2) and its candidate
     if (tuning) {
-        const int trial = b->tune_next;
-        const int cand = trial == 0 ? b->chosen : trial - 1;
-        if ((e = tc_set_launch(b->set, cand, b->stream, b->ev[0], b->ev[1])))
+        int p1 = b->p1, p2 = b->p2;
+        if (step >= 1 && step < 1 + TC_P1_CANDS * R) {
+            which = 1, cand = (step - 1) / R, p1 = cand;
+        } else if (step >= 1 + TC_P1_CANDS * R) {
+            which = 2, cand = (step - 1 - TC_P1_CANDS * R) / R, p2 = cand;
+        }
+        if ((e = tc_set_launch(b->set, p1, p2, b->stream, b->ev[0], b->ev[1], b->ev[2])))
             return b->err = std::string("set launch: ") + cudaGetErrorString(e), PANDA_ECUDA;
     } else {
         int rc = batch_graph(b);
@@ -1207,18 +1229,23 @@ int batch_chunk(panda_batch *b)
     if ((e = tc_set_gather(b->set, b->h_ctls, b->stream)) || (e = cudaStreamSynchronize(b->stream)))
         return b->err = std::string("set chunk: ") + cudaGetErrorString(e), PANDA_ECUDA;
     if (tuning) {
-        const int trial = b->tune_next++;
+        b->tune_step++;
         float ms = 0.0f;
-        if ((e = cudaEventElapsedTime(&ms, b->ev[0], b->ev[1])))
+        if (which > 0 && (e = cudaEventElapsedTime(&ms, b->ev[which - 1], b->ev[which])))
             return b->err = std::string("set timing: ") + cudaGetErrorString(e), PANDA_ECUDA;
-        if (trial > 0)
-            b->tune_ms[trial - 1] = ms;
-        if (trial == TC_SET_CANDS) {
-            int best = 0;
-            for (int q = 1; q < TC_SET_CANDS; ++q)
-                if (b->tune_ms[q] < b->tune_ms[best])
-                    best = q;
-            b->chosen = best;
+        const int rep = (step - 1) % R;
+        if (which == 1) {
+            b->p1_ms[cand][rep] = ms;
+            if (rep == R - 1)
+                b->p1_med[cand] = median3(b->p1_ms[cand]);
+            if (step == TC_P1_CANDS * R)  // the last phase-1 trial: keep the fastest
+                b->p1 = (int)(std::min_element(b->p1_med, b->p1_med + TC_P1_CANDS) - b->p1_med);
+        } else if (which == 2) {
+            b->p2_ms[cand][rep] = ms;
+            if (rep == R - 1)
+                b->p2_med[cand] = median3(b->p2_ms[cand]);
+            if (step == panda_batch::TUNE_STEPS - 1)
+                b->p2 = (int)(std::min_element(b->p2_med, b->p2_med + TC_P2_CANDS) - b->p2_med);
         }
     }
     return 0;
@@ -1312,7 +1339,7 @@ int panda_batch_create(panda_batch **out, int n, const int *T, const int *G, con
             e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
         if (!e)
             e = cudaMallocHost(&b->h_ctls, n * sizeof(Ctl));
-        for (int q = 0; q < 2 && !e; ++q)
+        for (int q = 0; q < 3 && !e; ++q)
             e = cudaEventCreate(&b->ev[q]);
         if (e) {
             std::string msg = std::string("panda_batch_create: set engine: ") + cudaGetErrorString(e);
@@ -1404,19 +1431,33 @@ panda_ctx *panda_batch_context(panda_batch *b, int k)
     return b->nets[k];
 }
 
-int panda_batch_schedule(const panda_batch *b, int *epi, float *trial_ms, int n_trials, int *done)
+int panda_batch_schedule(const panda_batch *b, int *p1, int *p2, float *p1_ms, int n1, float *p2_ms, int n2,
+                         int *done)
 {
     if (!b)
         return PANDA_EINVAL;
     if (!b->set)
         return 0;
-    if (epi)
-        *epi = TC_SET_EPI[b->chosen];
-    for (int q = 0; trial_ms && q < n_trials && q < TC_SET_CANDS; ++q)
-        trial_ms[q] = b->tune_ms[q];
+    if (p1)
+        *p1 = b->p1;
+    if (p2)
+        *p2 = b->p2;
+    for (int q = 0; p1_ms && q < n1 && q < TC_P1_CANDS; ++q)
+        p1_ms[q] = b->p1_med[q];
+    for (int q = 0; p2_ms && q < n2 && q < TC_P2_CANDS; ++q)
+        p2_ms[q] = b->p2_med[q];
     if (done)
-        *done = b->tune_next > TC_SET_CANDS;
-    return TC_SET_CANDS;
+        *done = b->tune_step >= panda_batch::TUNE_STEPS;
+    return 1;
+}
+
+const char *panda_batch_schedule_name(int phase, int k)
+{
+    if (phase == 1 && k >= 0 && k < TC_P1_CANDS)
+        return TC_P1_NAMES[k];
+    if (phase == 2 && k >= 0 && k < TC_P2_CANDS)
+        return TC_P2_NAMES[k];
+    return nullptr;
 }
 
 const char *panda_batch_last_error(const panda_batch *b) { return b ? b->err.c_str() : g_create_error.c_str(); }

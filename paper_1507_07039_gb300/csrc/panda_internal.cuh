@@ -221,12 +221,11 @@ void tc_release(Dev &d);
 cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
 
 // A set of networks (tensor-core modes, same options) iterated by one launch
-// per phase: phase 1 over every network's tiles, phase 2 persistent over an
-// LPT schedule of all their tiles, the norm and stop kernels over all their
-// rows.  Each network's W buffer is (parity + its iteration count) & 1.
-// Phase-2 schedules for TC_SET_CANDS epilogue weights are built; a tile's
-// result does not depend on which pair computes it, so any schedule gives the
-// same bits and the fastest can be picked by timing real iterations.
+// per phase: phases 1 and 2 persistent over LPT schedules of every network's
+// tiles, the norm and stop kernels over all their rows.  Each network's W
+// buffer is (parity + its iteration count) & 1.  A tile's result does not
+// depend on which pair computes it or when, so every schedule gives the same
+// bits and the fastest can be picked by timing real iterations.
 // C (Gp x Gp, FP32, row stride Gp) = Z . Z^T with the three-term BF16 split of
 // Z ([Gp][Kp] hi and lo, Gp a multiple of 256, Kp of 64) on CTA pairs; a
 // timed-out wait sets ST_TIMEOUT in ctl (device memory).
@@ -234,12 +233,18 @@ cudaError_t tc_gram(const __nv_bfloat16 *Zh, const __nv_bfloat16 *Zl, int Gp, in
                     cudaStream_t s);
 
 struct TcSet;
-constexpr int TC_SET_CANDS = 5;
-extern const int TC_SET_EPI[TC_SET_CANDS];
+// Schedule candidates of the set engine's autotuner: phase 1 (the order of each
+// network's tiles in the persistent pairs' LPT lists) and phase 2 (cost model,
+// epilogue weight, order of the LPT lists); TC_*_NAMES describe them.
+constexpr int TC_P1_CANDS = 2, TC_P2_CANDS = 5;
+extern const char *const TC_P1_NAMES[TC_P1_CANDS];
+extern const char *const TC_P2_NAMES[TC_P2_CANDS];
 cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out);
 cudaError_t tc_set_parity(TcSet *t, const std::vector<int> &parity, cudaStream_t s);
-// one iteration of every active network; events (may be NULL) around phase 2
-cudaError_t tc_set_launch(TcSet *t, int cand, cudaStream_t s, cudaEvent_t p2_begin, cudaEvent_t p2_end);
+// one iteration of every active network with phase-1 schedule p1 and phase-2
+// schedule p2; events (each may be NULL) before phase 1, before phase 2, after phase 2
+cudaError_t tc_set_launch(TcSet *t, int p1, int p2, cudaStream_t s, cudaEvent_t ev0, cudaEvent_t ev1,
+                          cudaEvent_t ev2);
 cudaError_t tc_set_gather(TcSet *t, Ctl *host, cudaStream_t s);  // all control blocks to host (async)
 void tc_set_destroy(TcSet *t);
 // D (M x N, row-major) = A (M x K) . B (N x K)^T through the tcgen05 pipeline,

@@ -76,7 +76,9 @@ def _load() -> ctypes.CDLL:
         "panda_batch_size": (i, [vp]),
         "panda_batch_context": (vp, [vp, i]),
         "panda_batch_last_error": (ctypes.c_char_p, [vp]),
-        "panda_batch_schedule": (i, [vp, pi, ctypes.POINTER(ctypes.c_float), i, pi]),
+        "panda_batch_schedule": (i, [vp, pi, pi, ctypes.POINTER(ctypes.c_float), i,
+                                     ctypes.POINTER(ctypes.c_float), i, pi]),
+        "panda_batch_schedule_name": (ctypes.c_char_p, [i, i]),
         "panda_batch_destroy": (None, [vp]),
         "panda_destroy": (None, [vp]),
     }
@@ -454,14 +456,25 @@ class PandaBatch:
         return ctypes.c_void_p(lib.panda_batch_context(self.h, int(k)))
 
     def schedule(self):
-        """(epilogue weight in use, trial times in ms, trials done) of the
-        phase-2 schedule autotuning; None for an FP32 batch."""
-        epi, done = ctypes.c_int(0), ctypes.c_int(0)
-        ms = (ctypes.c_float * 16)()
-        n = lib.panda_batch_schedule(self.h, ctypes.byref(epi), ms, 16, ctypes.byref(done))
+        """The schedule autotuning of a tensor-core batch: dict with the
+        phase-1 and phase-2 candidates in use (p1, p2), their descriptions,
+        the median trial times in ms of every candidate (p1_ms, p2_ms) and
+        whether the trials are over; None for an FP32 batch."""
+        p1, p2, done = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        m1, m2 = (ctypes.c_float * 16)(), (ctypes.c_float * 16)()
+        n = lib.panda_batch_schedule(self.h, ctypes.byref(p1), ctypes.byref(p2), m1, 16, m2, 16,
+                                     ctypes.byref(done))
         if n < 0:
             raise PandaError(n, "panda_batch_schedule")
-        return None if n == 0 else (epi.value, [ms[q] for q in range(n)], bool(done.value))
+        if n == 0:
+            return None
+        names = {ph: [] for ph in (1, 2)}
+        for ph in (1, 2):
+            while (nm := lib.panda_batch_schedule_name(ph, len(names[ph]))) is not None:
+                names[ph].append(nm.decode())
+        return {"p1": p1.value, "p2": p2.value, "p1_names": names[1], "p2_names": names[2],
+                "p1_ms": [m1[q] for q in range(len(names[1]))], "p2_ms": [m2[q] for q in range(len(names[2]))],
+                "done": bool(done.value)}
 
     def close(self):
         if self.h:

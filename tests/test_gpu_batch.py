@@ -1,8 +1,9 @@
 """Sets of networks (panda_batch_*): each network of an uneven set must match
 the same network run alone (bit for bit) and the FP64 oracle (needs a GB300).
 In the tensor-core modes the set runs as one launch per phase over every
-network's tiles, with the phase-2 schedule picked by timing real iterations;
-any schedule gives the same bits."""
+network's tiles (persistent CTA pairs over LPT lists), with the schedules of
+both phases picked by timing real iterations; any schedule gives the same
+bits."""
 from __future__ import annotations
 
 import os
@@ -59,15 +60,39 @@ def test_batch_runs_in_pieces(prec):
             _, it, _ = b.run(0.1, 0.0, chunk)
             done += np.asarray(it)
         got = [b.get(k) for k in range(len(b))]
-        epi, trial_ms, tuned = b.schedule()
+        sch = b.schedule()
     assert list(done) == list(iters1) == [40] * len(nets)
     for k in range(len(nets)):
         for a, g in zip(ref[k], got[k]):
             assert np.array_equal(a, g), f"network {k} differs"
-    # the trials ran (one iteration each) and the fastest schedule is the one in use
-    assert tuned and all(t > 0 for t in trial_ms)
-    weights = [48, 96, 192, 384, 768]
-    assert epi == weights[int(np.argmin(trial_ms))]
+    # every candidate of both phases was timed (median of three) and the fastest is in use
+    assert sch["done"] and len(sch["p1_names"]) == 2 and len(sch["p2_names"]) == 5
+    assert all(t > 0 for t in sch["p1_ms"]) and all(t > 0 for t in sch["p2_ms"])
+    assert sch["p1"] == int(np.argmin(sch["p1_ms"])) and sch["p2"] == int(np.argmin(sch["p2_ms"]))
+
+
+def test_batch_with_a_set_sized_network():
+    """A network of the set workload's size (250 TFs x 15000 genes, 100
+    samples from 10 factors) among small ones, two iterations on the set
+    engine: the big network against the FP64 oracle, every network against
+    its single run bit for bit."""
+    from paper_1507_07039_gb300 import panda
+    wl = synth.custom(250, 15000, synth.BASE_SEED + 1999, n_samples=100, n_factors=10, p_density=0.01)
+    nets = [synth.make_inputs(wl)] + uneven_set(3, seed=31)
+    with panda.PandaBatch(nets, prec=1) as b:
+        conv, iters, _ = b.run(0.1, 0.0, 2)
+        got = [b.get(k) for k in range(len(b))]
+    assert list(iters) == [2] * len(nets)
+    for k, (W0, P0, C0) in enumerate(nets):
+        single = gh.gpu_run(W0, P0, C0, 1, 0.1, 0.0, 2)
+        for a, g in zip((single["W"], single["P"], single["C"]), got[k]):
+            assert np.array_equal(a, g), f"network {k} differs from its single run"
+    orc = Oracle()
+    orc.set_threads(os.cpu_count() or 1)
+    W0, P0, C0 = nets[0]
+    o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 2)
+    e = gh.assert_parity({"W": got[0][0], "P": got[0][1], "C": got[0][2]}, o, 1, "250 x 15000 in a set")
+    print("\n250 x 15000 in a set, 2 iterations: " + ", ".join(f"{k} {v:.3e}" for k, v in e.items()))
 
 
 @pytest.mark.parametrize("prec", [1, 3])
