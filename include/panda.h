@@ -52,10 +52,10 @@ extern "C" {
  * PANDA_FP8MIX.  Under PANDA_BF16X3 and PANDA_BF16X2 the library holds C only
  * as the split pair the products read, hi = bf16(x) and lo = bf16(x - hi) of
  * each FP32 entry x, the same 4 bytes per entry as FP32 (the paper's remark
- * on memory after Eq. 9: one copy of the largest network, not two).  hi + lo
- * is within 2^-18 |x| of x, so C entries carry about 17 significant bits
- * instead of 24; panda_get and panda_get_state return hi + lo (exact in
- * FP32) with the diagonal from its FP64 vector. */
+ * on memory after Eq. 9: one copy of the largest network, not two).  BF16
+ * keeps 8 significant bits, so hi + lo is within 2^-16 |x| of x: C entries
+ * carry 16 significant bits instead of 24; panda_get and panda_get_state
+ * return hi + lo (exact in FP32) with the diagonal from its FP64 vector. */
 typedef enum {
     PANDA_FP32 = 0,   /* FP32 FFMA products (SIMT) */
     PANDA_BF16X3 = 1, /* tensor cores: x = hi + lo in BF16, hi*hi + hi*lo + lo*hi, FP32 accumulation */
@@ -117,7 +117,7 @@ int panda_create_device(panda_ctx **out, int T, int G, const float *dW0, const f
  * across the N samples of X (G x N, row-major host array, gene g's samples in
  * X[g*N .. g*N + N-1]), unit diagonal.  Each gene's centred samples are scaled
  * to unit norm in FP64 and the correlations are their Gram matrix on the
- * tensor cores (BF16 three-term split, FP32 accumulation: within 1.2e-5 of
+ * tensor cores (BF16 three-term split, FP32 accumulation: within 4.6e-5 of
  * the exact correlation, about 1e-6 with hundreds of samples), upper triangle mirrored so C0 is exactly symmetric.
  * P0 may be NULL: the identity (no interaction data).  Errors as panda_create,
  * plus PANDA_EDEGENERATE when a gene has zero variance across the samples,

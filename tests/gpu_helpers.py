@@ -122,6 +122,25 @@ def assert_parity(g, o, prec=0, what="", tol=None):
     return e
 
 
+def _bf16_rne(x: np.ndarray) -> np.ndarray:
+    """FP32 values rounded to BF16 (nearest even), returned as FP32."""
+    u = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def split_held(X: np.ndarray) -> np.ndarray:
+    """What a BF16X3 or BF16X2 context returns for a C it holds as the split
+    pair hi = bf16(x), lo = bf16(x - hi): hi + lo (exact in FP32) off the
+    diagonal, the diagonal as given (it is kept in FP64)."""
+    x = np.ascontiguousarray(X, np.float32)
+    hi = _bf16_rne(x)
+    lo = _bf16_rne(x - hi)
+    out = hi + lo
+    np.fill_diagonal(out, np.diag(x))
+    return out
+
+
 def inputs(name_or_wl):
     wl = synth.get(name_or_wl) if isinstance(name_or_wl, str) else name_or_wl
     return synth.make_inputs(wl)

@@ -113,10 +113,10 @@ def test_normalized_state_matches_oracle(orc, panda, name, offset, prec):
     with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:
         gW, gP, gC = ctx.get()
     nets = (("W", gW, oW), ("P", gP, oP), ("C", gC, oC))
-    if prec == 1:  # BF16X3 holds C as hi + lo of the FP32 Z-score: within 2^-18 |x| of it
+    if prec == 1:  # BF16X3 holds C as hi + lo of the FP32 Z-score: within 2^-16 |x| of it
         o32 = oC.astype(np.float32).astype(np.float64)
         off = ~np.eye(oC.shape[0], dtype=bool)
-        assert np.all(np.abs(gC.astype(np.float64) - o32)[off] <= 2.0 ** -17 * np.abs(o32)[off])
+        assert np.all(np.abs(gC.astype(np.float64) - o32)[off] <= 2.0 ** -16 * np.abs(o32)[off])
         dg, do = np.diag(gC), np.diag(oC).astype(np.float32)  # the diagonal: from its FP64 vector
         assert np.all(np.abs(dg.astype(np.float64) - do) <= np.spacing(np.maximum(np.abs(dg), np.abs(do))))
         nets = nets[:2]
@@ -313,7 +313,9 @@ def test_validation_finds_every_position(panda, prec, T, G):
     C0 = gh.random_symmetric(rng, G)
     with panda.PandaContext(W0, P0, C0, prec=prec, normalize=False) as ctx:
         gW, gP, gC = ctx.get()
-    assert np.array_equal(gW, W0) and np.array_equal(gP, P0) and np.array_equal(gC, C0)
+    # BF16X3 holds C as its split pair: hi + lo of each entry, the diagonal exact
+    assert np.array_equal(gW, W0) and np.array_equal(gP, P0)
+    assert np.array_equal(gC, gh.split_held(C0) if prec == 1 else C0)
 
     def expect(code, W=W0, P=P0, C=C0):
         with pytest.raises(panda.PandaError) as e:
