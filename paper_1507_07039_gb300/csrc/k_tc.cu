@@ -68,6 +68,7 @@ struct SetArgs {
     const int *parity;     // W buffer of a network = (parity + its iteration count) & 1
     const int4 *items1;    // phase 1: (network, mt, nt, cost) tiles, listed per CTA pair
     const int *p1_off;     // phase 1: per CTA pair, its range of items1
+    float *acc;            // phase 1: per CTA, its running-sum slot (128 x 256 floats)
     const int *sched_off;  // phase 2: per CTA pair, its range of sched
     const int *sched;      // phase 2: packed tiles (as for one network)
     const int *sched_net;  // phase 2: the network of each tile
@@ -495,17 +496,34 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 // (grid x = 2 x T tiles, y = G tiles).  CTA r loads rows 128 r .. + 127 of
 // the tile's A blocks (P_off for R, W for A) and of its B blocks (columns of W
 // for R, C_off for A); the even CTA issues cta_group::2 MMAs into two TMEM
-// accumulators of 256 columns (R at column 0, A at column 256).  Warps:
-// 0 TMA, 1 MMA (even CTA), 2-9 epilogue (two per TMEM lane quarter, each
-// taking 128 of the 256 columns in 16-column sub-chunks).
+// buffers of 256 columns: A-num in chunks alternating between them (drained
+// by the epilogue warps into a running sum, see P1_CHUNK), then R-num in the
+// buffer the last chunk leaves free.  Warps: 0 TMA, 1 MMA (even CTA), 2-9
+// epilogue (two per TMEM lane quarter, each taking 128 of the 256 columns in
+// 16-column sub-chunks).
 // ---------------------------------------------------------------------------
 constexpr int ST1 = 3;
 constexpr uint32_t STAGE1 = 4 * A_BYTES;   // per CTA: A hi, A lo, B hi, B lo (128 rows each)
 constexpr int EPI1 = 8, THREADS1 = 64 + 32 * EPI1;
 
+// The availability numerator W.C_off runs over all genes (K up to 46080).
+// The tensor core's FP32 accumulation loses low bits toward zero on every
+// MMA, so a long chain of MMAs into one accumulator drifts: measured, for
+// sums of positive products, -3.7e-6 relative at K = 1024 and -1.1e-4 at
+// K = 17152 (a sequential FP32 sum: -7e-8).  So A-num is summed in chunks of
+// P1_CHUNK k-blocks, each into a fresh accumulator; the two TMEM buffers
+// alternate between chunks, the epilogue warps (idle during the main loop)
+// add each finished chunk into a running FP32 sum in global memory (this
+// CTA's own 128 x 256 slot, L2-resident), and R-num, which is short, runs
+// last in the buffer the chunks leave free.
+constexpr int P1_CHUNK = 16;
+constexpr size_t P1_SLOT = 128 * 256;  // floats of one CTA's running-sum slot
+
 struct Sync1 {
     uint64_t full[ST1], empty[ST1];
     uint64_t accum;
+    uint64_t chunk_done[2];  // MMA -> epilogue: an A-num chunk in TMEM buffer b is complete
+    uint64_t buf_free[2];    // epilogue warps of both CTAs -> MMA issuer: buffer b has been drained
     uint32_t tmem;
     int abort, issued, consumed;
 };
@@ -542,6 +560,10 @@ __device__ __forceinline__ void phase1_tmem_alloc()
             mbar_init(&sy.empty[q], 1);
         }
         mbar_init(&sy.accum, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&sy.chunk_done[b], 1);
+            mbar_init(&sy.buf_free[b], 2 * EPI1);
+        }
         sy.abort = 0;
         fence_mbar_init();
     }
@@ -563,12 +585,14 @@ __device__ __forceinline__ void phase1_tmem_free()
 
 // The body of phase 1 for the tile (mt, nt) of one network: maps and d are
 // that network's (kernel parameters for one network, entries of arrays in
-// global memory for a set), cur its current W buffer.  g counts the pipeline
-// stages and tile the tiles this CTA has run before (barrier phases follow
-// them); both advance here.  Both CTAs of the pair run every call together and
-// end it at a cluster barrier, after which TMEM is free for the next tile.
+// global memory for a set), cur its current W buffer, scr this CTA's slot of
+// 128 x 256 floats for the running A-num sum ([column][row]).  g counts the
+// pipeline stages, tile the tiles and u[b] the drains of TMEM buffer b this CTA
+// has run before (barrier phases follow them); all advance here.  Both CTAs of
+// the pair run every call together and end it at a cluster barrier, after
+// which TMEM is free for the next tile.
 __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, int cur, int mt, int nt, int &g,
-                                            int &tile)
+                                            int &tile, int (&u)[2], float *scr)
 {
     Ctl *ctl = d.ctl;
     if (!ctl->active)  // both CTAs of a pair see the same value and leave together
@@ -586,13 +610,20 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
     const uint32_t rank = cluster_ctarank();
     const int m0 = mt * 256 + 128 * (int)rank;  // this CTA's 128 rows (TFs)
     const int n0 = nt * 256;                    // the tile's 256 columns (genes)
-    // k-blocks: R-num over TFs (64 BF16 per row), then A-num over genes (64 BF16, or 128 E4M3 under FP8MIX)
-    const int nR = d.Tp / BK, nk = nR + d.Gp / (d.fp8 ? 2 * BK : BK);
+    // k-blocks kb: R-num over TFs (kb < nR, 64 BF16 per row) and A-num over genes (kb >= nR, 64 BF16,
+    // or 128 E4M3 under FP8MIX).  They are issued in the order s = 0 .. nk - 1: first A-num in nc
+    // chunks of P1_CHUNK k-blocks (chunk c in TMEM buffer c & 1), then R-num (buffer nc & 1).
+    const int nR = d.Tp / BK, nA = d.Gp / (d.fp8 ? 2 * BK : BK), nk = nR + nA;
+    const int nc = (nA + P1_CHUNK - 1) / P1_CHUNK, bR = nc & 1;
+    auto kb_of = [nR, nA](int s) { return s < nA ? nR + s : s - nA; };
 
     const int g0 = g;      // stages run by this CTA before this tile
     const uint32_t tpar = (uint32_t)tile & 1u;  // phase of the accumulator barrier for this tile
+    const int u0[2] = {u[0], u[1]};  // drains of each buffer before this tile
     g += nk;
     ++tile;
+    u[0] += nc / 2;        // chunks 0, 2, .. < nc - 1 are drained from buffer 0
+    u[1] += (nc - 1) / 2;  // chunks 1, 3, .. < nc - 1 from buffer 1
     if (threadIdx.x == 0) {
         sy.issued = 0;
         sy.consumed = 0;
@@ -602,10 +633,10 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
     if (warp == 0) {
         if (lane == 0) {  // ---- TMA producer (both CTAs; completion counted on the even CTA) ----
             const int nb0 = n0 + 128 * (int)rank;  // this CTA's half of the B rows
-            int kb = 0;
-            for (; kb < nk; ++kb) {
-                const int st = (g0 + kb) % ST1;
-                if (!wait_bounded(&sy.empty[st], ((uint32_t)((g0 + kb) / ST1) & 1u) ^ 1u, &sy.abort, ctl))
+            int s = 0;
+            for (; s < nk; ++s) {
+                const int kb = kb_of(s), st = (g0 + s) % ST1;
+                if (!wait_bounded(&sy.empty[st], ((uint32_t)((g0 + s) / ST1) & 1u) ^ 1u, &sy.abort, ctl))
                     break;
                 const uint32_t fb = mapa_shared(smem_u32(&sy.full[st]), 0);
                 if (rank == 0)  // both CTAs' tiles: 4 per CTA, 3 without B's lo half, 2 of E4M3
@@ -643,26 +674,38 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                     }
                 }
             }
-            sy.issued = kb;
+            sy.issued = s;
         }
     } else if (warp == 1) {
         if (lane == 0 && rank == 0) {  // ---- MMA issuer of the pair ----
             constexpr uint32_t idesc = idesc_bf16_f32(256, 256);
-            int kb = 0;
-            for (; kb < nk; ++kb) {
-                const int st = (g0 + kb) % ST1;
-                if (!wait_bounded(&sy.full[st], (uint32_t)((g0 + kb) / ST1) & 1u, &sy.abort, ctl))
+            int s = 0;
+            for (; s < nk; ++s) {
+                const int kb = kb_of(s), st = (g0 + s) % ST1;
+                // this k-block's accumulator: A-num chunk c in buffer c & 1, R-num in buffer bR; a buffer
+                // is written again only once the epilogue has drained the chunk it held two chunks before
+                const int a = kb - nR, c = a / P1_CHUNK;
+                const int buf = kb >= nR ? (c & 1) : bR;
+                const bool fresh = kb >= nR ? a % P1_CHUNK == 0 : kb == 0;
+                const int prev = kb >= nR ? c - 2 : nc - 2;  // chunk that last used buf (< 0: none)
+                if (fresh && prev >= 0 &&
+                    !wait_bounded(&sy.buf_free[buf], (uint32_t)(u0[buf] + (prev >> 1)) & 1u, &sy.abort, ctl))
+                    break;
+                if (!wait_bounded(&sy.full[st], (uint32_t)((g0 + s) / ST1) & 1u, &sy.abort, ctl))
                     break;
                 tc_fence_after();
                 const uint32_t base = smem_u32(stages + (size_t)st * STAGE1);
-                const uint32_t dacc = sy.tmem + (kb < nR ? 0u : 256u);
-                const bool fresh = kb == 0 || kb == nR;
+                const uint32_t dacc = sy.tmem + (uint32_t)buf * 256u;
+                // a chunk other than the last ends: the epilogue drains it into the running sum
+                const bool chunk_end = kb >= nR && c < nc - 1 && (a % P1_CHUNK == P1_CHUNK - 1);
                 if (kb >= nR && d.fp8) {
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)  // K = 32 per MMA
                         mma_e4m3_pair(dacc, sdesc_k_sw128(base + kk * 32), sdesc_k_sw128(base + A_BYTES + kk * 32),
                                       idesc_e4m3_f32(256, 256), (fresh && kk == 0) ? 0u : 1u);
                     mma_commit_pair(&sy.empty[st]);
+                    if (chunk_end)
+                        mma_commit_pair(&sy.chunk_done[buf]);
                     continue;
                 }
                 const bool bmn = kb < nR || (kb - nR) * BK < n0;  // B block loaded MN-major
@@ -682,8 +725,10 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                     mma_bf16_pair(dacc, al, bh, id, 1u);
                 }
                 mma_commit_pair(&sy.empty[st]);
+                if (chunk_end)
+                    mma_commit_pair(&sy.chunk_done[buf]);
             }
-            sy.consumed = kb;
+            sy.consumed = s;
             mma_commit_pair(&sy.accum);  // also on abort, so the epilogues can drain
         }
     } else {  // ---- epilogue: warps 2..9 of both CTAs ----
@@ -714,11 +759,36 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
         float nxt[16];
         ld16(wrow, nxt);
         epi_bar2();
-        const bool live = wait_bounded(&sy.accum, tpar, &sy.abort, ctl) && !*(volatile int *)&sy.abort;
+        const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
+        // while the MMAs run on: add each finished A-num chunk but the last into the running sum
+        // (this thread's row r, its 128 columns; [column][row] so a warp's accesses are contiguous)
+        bool live = true;
+        const uint32_t bfree_even = mapa_shared(smem_u32(&sy.buf_free[0]), 0);
+        for (int c = 0; c + 1 < nc && live; ++c) {
+            const int b = c & 1;
+            live = wait_bounded(&sy.chunk_done[b], (uint32_t)(u0[b] + (c >> 1)) & 1u, &sy.abort, ctl) &&
+                   !*(volatile int *)&sy.abort;
+            tc_fence_after();
+            if (!live)
+                break;
+#pragma unroll 1
+            for (int j = 0; j < 8; ++j) {
+                float v[16];
+                tmem_ld16(trow + (uint32_t)b * 256u + half * 128 + j * 16, v);
+                float *sp = scr + (size_t)(half * 128 + j * 16) * 128 + r;
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    sp[q * 128] = c == 0 ? v[q] : sp[q * 128] + v[q];
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0)  // this warp is done with the buffer: tell the even CTA's MMA issuer
+                mbar_arrive_cluster(bfree_even + (uint32_t)b * (uint32_t)sizeof(uint64_t));
+        }
+        live = live && wait_bounded(&sy.accum, tpar, &sy.abort, ctl) && !*(volatile int *)&sy.abort;
         tc_fence_after();
         const float a = ctl->alpha, keep = 1.0f - a, halfa = 0.5f * a;
         float rowsq = 0.0f, hsum = 0.0f;
-        const uint32_t trow = sy.tmem + ((uint32_t)(wq * 32) << 16);
 #pragma unroll 1
         for (int c = 0; c < 8 && live; ++c) {
             const int cc = half * 128 + c * 16, j0 = n0 + cc;
@@ -728,8 +798,13 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                 w[q] = nxt[q];
             if (c < 7)
                 ld16(wrow + (c + 1) * 16, nxt);  // next sub-chunk's W, in flight meanwhile
-            tmem_ld16(trow + cc, rr);
-            tmem_ld16(trow + 256 + cc, aa);
+            tmem_ld16(trow + (uint32_t)bR * 256u + cc, rr);
+            tmem_ld16(trow + (uint32_t)(bR ^ 1) * 256u + cc, aa);  // the last A-num chunk
+            if (nc > 1) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q)
+                    aa[q] = scr[(size_t)(cc + q) * 128 + r] + aa[q];
+            }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
                 wn[q] = 0.0f;
@@ -815,8 +890,8 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
     tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0 && rank == 0)  // loads counted here but not consumed (abort only)
-        for (int kb = sy.consumed; kb < sy.consumed + ST1 && kb < sy.issued; ++kb)
-            wait_bounded(&sy.full[(g0 + kb) % ST1], (uint32_t)((g0 + kb) / ST1) & 1u, &sy.abort, ctl, true);
+        for (int s = sy.consumed; s < sy.consumed + ST1 && s < sy.issued; ++s)
+            wait_bounded(&sy.full[(g0 + s) % ST1], (uint32_t)((g0 + s) / ST1) & 1u, &sy.abort, ctl, true);
     cluster_sync();  // neither CTA goes on while the pair may still signal it
 }
 
@@ -828,8 +903,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
     if (!d.ctl->active)  // both CTAs of a pair see the same value and leave together
         return;
     phase1_tmem_alloc();
-    int g = 0, tile = 0;
-    phase1_tile(maps, d, cur, blockIdx.x >> 1, blockIdx.y, g, tile);
+    int g = 0, tile = 0, u[2] = {0, 0};
+    float *scr = d.p1_acc + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * P1_SLOT;
+    phase1_tile(maps, d, cur, blockIdx.x >> 1, blockIdx.y, g, tile, u, scr);
     phase1_tmem_free();
 }
 
@@ -840,10 +916,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1) k_tc_ph
 {
     const int pair = blockIdx.x >> 1;
     phase1_tmem_alloc();
-    int g = 0, tile = 0;
+    int g = 0, tile = 0, u[2] = {0, 0};
+    float *scr = a.acc + (size_t)blockIdx.x * P1_SLOT;
     for (int q = a.p1_off[pair]; q < a.p1_off[pair + 1]; ++q) {
         const int4 w = a.items1[q];  // (network, mt, nt, cost)
-        phase1_tile(a.maps[w.x], a.devs[w.x], set_cur(a, w.x), w.y, w.z, g, tile);
+        phase1_tile(a.maps[w.x], a.devs[w.x], set_cur(a, w.x), w.y, w.z, g, tile, u, scr);
     }
     phase1_tmem_free();
 }
@@ -1739,6 +1816,7 @@ struct TcSet {
     int2 *blocks = nullptr;
     int nblocks = 0;
     Ctl *gather = nullptr;
+    float *acc = nullptr;     // phase 1: one running-sum slot per persistent CTA
     struct P1 {               // a phase-1 schedule: per pair, a list of (network, mt, nt, cost)
         int4 *items = nullptr;
         int *off = nullptr;
@@ -1787,7 +1865,8 @@ cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out)
     if (!(e = cudaGetDevice(&dev)) && !(e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) &&
         !(e = upload(&t->devs, hd)) && !(e = upload(&t->maps, hm)) && !(e = upload(&t->blocks, bl)) &&
         !(e = cudaMalloc(&t->parity, t->n * sizeof(int))) && !(e = cudaMemset(t->parity, 0, t->n * sizeof(int))) &&
-        !(e = cudaMalloc(&t->gather, t->n * sizeof(Ctl)))) {
+        !(e = cudaMalloc(&t->gather, t->n * sizeof(Ctl))) &&
+        !(e = cudaMalloc(&t->acc, sizeof(float) * P1_SLOT * (size_t)(nsm & ~1)))) {
         t->pairs = nsm / 2;
         for (int q = 0; q < TC_P1_CANDS && !e; ++q) {  // phase 1: persistent pairs over LPT lists
             std::vector<std::pair<long long, int4>> all;
@@ -1835,7 +1914,7 @@ cudaError_t tc_set_launch(TcSet *t, int p1, int p2, cudaStream_t s, cudaEvent_t 
 {
     const TcSet::P1 &a1 = t->p1[p1];
     const TcSet::P2 &c = t->p2[p2];
-    SetArgs a{t->devs, t->maps, t->parity, a1.items, a1.off, c.off, c.tiles, c.nets};
+    SetArgs a{t->devs, t->maps, t->parity, a1.items, a1.off, t->acc, c.off, c.tiles, c.nets};
     if (ev0)
         cudaEventRecord(ev0, s);
     k_tc_phase1_set<<<2 * t->pairs, THREADS1, phase1_smem(), s>>>(a);
@@ -1869,6 +1948,7 @@ void tc_set_destroy(TcSet *t)
     cudaFree(t->parity);
     cudaFree(t->blocks);
     cudaFree(t->gather);
+    cudaFree(t->acc);
     for (auto &c : t->p1) {
         cudaFree(c.items);
         cudaFree(c.off);

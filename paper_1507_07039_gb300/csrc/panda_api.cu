@@ -178,6 +178,7 @@ int plan_memory(panda_ctx *c)
         }
         DALLOC(d.Ph, Tp * Tp);
         DALLOC(d.Pl, Tp * Tp);
+        DALLOC(d.p1_acc, (Tp / 256) * (Gp / 256) * 2 * (size_t)128 * 256);  // phase 1: per CTA
         if (d.fp8) {  // W.C and W^T.W on E4M3 copies; no BF16 copy of C
             for (int b = 0; b < 2; ++b) {
                 DALLOC(d.W8[b], Tp * Gp);

@@ -86,6 +86,8 @@ struct Dev {
     unsigned *f8n;               // squared-norm maxima (float bits): [0..3] this iteration's
                                  // (rsqP, csqC, rsqW, csqW), [4..7] the state's, latched
     void *tc_host;               // host-side tensor maps of the split copies (tensor-core path)
+    float *p1_acc;               // tensor-core phase 1: per CTA of its grid, a 128 x 256 slot for the
+                                 // running sum of the availability numerator's chunks
 };
 
 // Largest power of two s with s * bound <= 448 (the largest finite E4M3 value):
