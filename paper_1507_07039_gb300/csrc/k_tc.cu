@@ -217,6 +217,16 @@ __device__ __forceinline__ void ld_rows4(const float *p, int ld, float4 (&v)[4])
         v[i] = *reinterpret_cast<const float4 *>(p + (size_t)(8 * i) * ld);
 }
 
+// 8 bytes from global memory, asking L2 to fetch the whole 128-byte line: a
+// warp's row segments here are 32 bytes, and the next sub-chunk reads the
+// rest of each line
+__device__ __forceinline__ uint2 ld8_l2line(const void *p)
+{
+    uint2 v;
+    asm volatile("ld.global.L2::128B.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    return v;
+}
+
 // As ld_rows4 for a matrix held as a BF16 split pair: four values hi + lo from
 // 8-byte loads of each half (the sum is exact in FP32)
 __device__ __forceinline__ void ld_rows4_split(const __nv_bfloat16 *h, const __nv_bfloat16 *l, int ld, float4 (&v)[4])
@@ -224,7 +234,7 @@ __device__ __forceinline__ void ld_rows4_split(const __nv_bfloat16 *h, const __n
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const size_t o = (size_t)(8 * i) * ld;
-        const uint2 a = *reinterpret_cast<const uint2 *>(h + o), b = *reinterpret_cast<const uint2 *>(l + o);
+        const uint2 a = ld8_l2line(h + o), b = ld8_l2line(l + o);
         const float2 a0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.x));
         const float2 a1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.y));
         const float2 b0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&b.x));
