@@ -527,6 +527,14 @@ constexpr int EPI1 = 8, THREADS1 = 64 + 32 * EPI1;
 // CTA's own 128 x 256 slot, L2-resident), and R-num, which is short, runs
 // last in the buffer the chunks leave free.
 constexpr int P1_CHUNK = 16;
+
+// v added into a running-sum entry in L2 without a round trip (the entry's
+// earlier chunks were written by this same thread, so the adds of one entry
+// happen in chunk order: the sum is deterministic)
+__device__ __forceinline__ void red_add(float *p, float v)
+{
+    asm volatile("red.relaxed.gpu.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
 constexpr size_t P1_SLOT = 128 * 256;  // floats of one CTA's running-sum slot
 
 struct Sync1 {
@@ -786,9 +794,15 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                 float v[16];
                 tmem_ld16(trow + (uint32_t)b * 256u + half * 128 + j * 16, v);
                 float *sp = scr + (size_t)(half * 128 + j * 16) * 128 + r;
+                if (c == 0) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    sp[q * 128] = c == 0 ? v[q] : sp[q * 128] + v[q];
+                    for (int q = 0; q < 16; ++q)
+                        sp[q * 128] = v[q];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        red_add(sp + q * 128, v[q]);
+                }
             }
             tc_fence_before();
             __syncwarp();
@@ -813,7 +827,7 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
             if (nc > 1) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    aa[q] = scr[(size_t)(cc + q) * 128 + r] + aa[q];
+                    aa[q] = __ldcg(scr + (size_t)(cc + q) * 128 + r) + aa[q];  // L2: where the adds landed
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -968,6 +982,40 @@ struct P2Cfg {
     static constexpr size_t BLK = 32 * 17;             // per epilogue warp: 32 x 16 staging block (padded)
 };
 
+// A scheduled phase-2 item.  A C tile (bit 31 clear: bits 16-30 row block,
+// 0-15 column block) is one item over all of its K (TFs).  A P tile's K runs
+// over all genes, so, like phase 1's availability product, it is summed in
+// chunks of P1_CHUNK k-blocks, each into a fresh accumulator: the tile is
+// scheduled as consecutive items on one CTA pair (bit 31 set: bits 24-30 the
+// chunk, 16-23 row block, 0-15 column block); the epilogue adds every chunk
+// but the last into the CTA's running-sum slot and finishes the tile on the
+// last.
+struct P2Item {
+    bool isP;
+    int bm, bn, kb0, kb1, chunk, nchunks;
+};
+__host__ __device__ inline int p2_chunks(const Dev &d) { return (d.Gp / BK + P1_CHUNK - 1) / P1_CHUNK; }
+__device__ __forceinline__ P2Item p2_item(int tile, const Dev &d)
+{
+    P2Item it;
+    it.isP = tile < 0;
+    it.bn = tile & 0xffff;
+    if (it.isP) {
+        it.bm = (tile >> 16) & 0xff;
+        it.chunk = (tile >> 24) & 0x7f;
+        it.nchunks = p2_chunks(d);
+        it.kb0 = it.chunk * P1_CHUNK;
+        it.kb1 = min(d.Gp / BK, it.kb0 + P1_CHUNK);
+    } else {
+        it.bm = (tile >> 16) & 0x7fff;
+        it.chunk = 0;
+        it.nchunks = 1;
+        it.kb0 = 0;
+        it.kb1 = d.Tp / (d.fp8 ? 2 * BK : BK);
+    }
+    return it;
+}
+
 template <int ST>
 struct Sync2T {
     uint64_t full[ST], empty[ST];
@@ -991,6 +1039,7 @@ struct P2One {
     const Dev &d;
     int c;
     const int *off, *tiles;
+    __device__ float *scratch() const { return d.p1_acc + (size_t)blockIdx.x * P1_SLOT; }
     __device__ int net(int) const { return 0; }
     __device__ const Dev &dev(int) const { return d; }
     __device__ const TcMaps &maps(int) const { return m; }
@@ -1000,6 +1049,7 @@ struct P2One {
 struct P2Set {
     const SetArgs &a;
     const int *off, *tiles;
+    __device__ float *scratch() const { return a.acc + (size_t)blockIdx.x * P1_SLOT; }
     __device__ int net(int n) const { return a.sched_net[n]; }
     __device__ const Dev &dev(int k) const { return a.devs[k]; }
     __device__ const TcMaps &maps(int k) const { return a.maps[k]; }
@@ -1062,16 +1112,15 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 const Dev &d = src.dev(net);
                 const TcMaps &maps = src.maps(net);
                 const int cur = src.cur(net);
-                const int tile = src.tiles[n];
-                const bool isP = tile < 0;
-                const int m0 = ((tile >> 16) & 0x7fff) * N2 + 128 * rank, n0 = (tile & 0xffff) * N2 + 128 * rank;
+                const P2Item it = p2_item(src.tiles[n], d);
+                const bool isP = it.isP;
+                const int m0 = it.bm * N2 + 128 * rank, n0 = it.bn * N2 + 128 * rank;
                 const bool q8 = d.fp8 && !isP;  // FP8MIX: C tiles from the E4M3 copy of W'^T, one term
-                const int nk = isP ? d.Gp / BK : d.Tp / (q8 ? 2 * BK : BK);
                 // P tiles: rows of W' (K over genes, K-major); C tiles: columns of W' (K over TFs),
                 // read from the same arrays MN-major
                 const CUtensorMap *mh = isP ? &maps.Wh[cur] : &maps.Whm[cur];
                 const CUtensorMap *ml = isP ? &maps.Wl[cur] : &maps.Wlm[cur];
-                for (int kb = 0; kb < nk; ++kb, ++g) {
+                for (int kb = it.kb0; kb < it.kb1; ++kb, ++g) {
                     const int st = g % ST2;
                     if (!wait_bounded(&sy.empty[st], ((uint32_t)(g / ST2) & 1u) ^ 1u, &sy.abort, d.ctl)) {
                         ok = false;
@@ -1118,14 +1167,15 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 ++idx;
                 const Dev &d = src.dev(net);
                 const int tile = src.tiles[n];
+                const P2Item it = p2_item(tile, d);
                 const bool q8 = d.fp8 && tile >= 0;
-                const int nk = tile < 0 ? d.Gp / BK : d.Tp / (q8 ? 2 * BK : BK);
                 const int buf = idx & 1;
                 if (!wait_bounded(&sy.tempty[buf], ((uint32_t)(idx >> 1) & 1u) ^ 1u, &sy.abort, d.ctl))
                     break;
                 tc_fence_after();
                 const uint32_t dacc = sy.tmem + buf * N2;
-                for (int kb = 0; kb < nk; ++kb, ++g) {
+                for (int kb = it.kb0; kb < it.kb1; ++kb, ++g) {
+                    const bool first = kb == it.kb0;  // a fresh accumulator for every item
                     const int st = g % ST2;
                     if (!wait_bounded(&sy.full[st], (uint32_t)(g / ST2) & 1u, &sy.abort, d.ctl)) {
                         ok = false;
@@ -1138,7 +1188,7 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                         for (int kk = 0; kk < 4; ++kk)  // K = 32 per MMA
                             mma_e4m3_pair(dacc, sdesc_k_sw128(base + kk * 32),
                                           sdesc_k_sw128(base + A_BYTES + kk * 32), idesc_e4m3_f32(256, N2),
-                                          (kb == 0 && kk == 0) ? 0u : 1u);
+                                          (first && kk == 0) ? 0u : 1u);
                         mma_commit_pair(&sy.empty[st]);
                         continue;
                     }
@@ -1155,10 +1205,10 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                         const uint64_t bl = mn ? sdesc_mn_sw128(base + 3 * A_BYTES + moff, A_BYTES / 2)
                                                : sdesc_k_sw128(base + 3 * A_BYTES + off);
                         if (d.split_b) {  // hi(A) once from shared memory for hi.hi and hi.lo
-                            mma_bf16_pair_fill_a(dacc, ah, bh, id, (kb == 0 && kk == 0) ? 0u : 1u);
+                            mma_bf16_pair_fill_a(dacc, ah, bh, id, (first && kk == 0) ? 0u : 1u);
                             mma_bf16_pair_lastuse_a(dacc, ah, bl, id, 1u);
                         } else {
-                            mma_bf16_pair(dacc, ah, bh, id, (kb == 0 && kk == 0) ? 0u : 1u);
+                            mma_bf16_pair(dacc, ah, bh, id, (first && kk == 0) ? 0u : 1u);
                         }
                         mma_bf16_pair(dacc, al, bh, id, 1u);
                     }
@@ -1177,12 +1227,43 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
         float *blk = blocks + (size_t)e * Cfg::BLK;  // this warp's 32 x 16 staging block, rows of 17
         const int tt = threadIdx.x - 64;  // 0..383
         const uint32_t tempty_even = mapa_shared(smem_u32(&sy.tempty[0]), 0);
+        float *scr = src.scratch();  // running sums of P tiles' K chunks ([column][row])
         for (int n = first, idx = -1; n < last; ++n) {
             const int net = src.net(n);
             if (!src.active(net))
                 continue;
             ++idx;
             const Dev &d = src.dev(net);
+            const P2Item it = p2_item(src.tiles[n], d);
+            if (it.chunk + 1 < it.nchunks) {  // a P tile's K chunk before the last: into the running sum
+                const int buf = idx & 1;
+                const bool ok = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, d.ctl) &&
+                                !*(volatile int *)&sy.abort;
+                tc_fence_after();
+                if (ok) {
+                    const uint32_t tb = sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16);
+#pragma unroll 1
+                    for (int c = c_begin; c < c_end; ++c) {  // this warp's 16-column sub-chunks
+                        float v[16];
+                        tmem_ld16(tb + c * 16, v);
+                        float *sp = scr + (size_t)(c * 16) * 128 + r;
+                        if (it.chunk == 0) {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                sp[q * 128] = v[q];
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 16; ++q)
+                                red_add(sp + q * 128, v[q]);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0)
+                        mbar_arrive_cluster(tempty_even + buf * (uint32_t)sizeof(uint64_t));
+                }
+                continue;
+            }
             const int cur = src.cur(net);
             const float a = d.ctl->alpha, keep = 1.0f - a;
             // FP8MIX: C-tile accumulators hold products of W'^T scaled by f8[cur] on both sides; C' gets
@@ -1192,9 +1273,8 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 d.fp8 ? e4m3_scale(fp8_bound_c(__uint_as_float(d.f8n[5]), __uint_as_float(d.f8n[3]))) : 1.0f;
             if (d.fp8 && threadIdx.x == 64)
                 d.f8[2] = sC;  // the scale of C8 from here on (every writer stores the same value)
-            const int tile = src.tiles[n];
-            const bool isP = tile < 0;
-            const int bm = (tile >> 16) & 0x7fff, bn = tile & 0xffff;
+            const bool isP = it.isP;
+            const int bm = it.bm, bn = it.bn;
             const int m0 = bm * N2 + 128 * (int)rank, n0 = bn * N2;
             const int nn = isP ? d.T : d.G, ld = isP ? d.Tp : d.Gp;
             const int nbk = ceil_div(ld, N2);  // 256-blocks: the column-role slots start here
@@ -1267,6 +1347,11 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
                     acc[q] = __uint_as_float(accr[q]) * ascale;
+                if (it.nchunks > 1) {  // a P tile's last K chunk: add the running sum of the others
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        acc[q] = __ldcg(scr + (size_t)(cc + q) * 128 + r) + acc[q];  // L2: where the adds landed
+                }
                 if (c + 1 == c_end) {  // this warp is done with the accumulator: tell the even CTA
                     tc_fence_before();
                     __syncwarp();
@@ -1635,7 +1720,9 @@ struct P2Spec {
 };
 const P2Spec TC_P2_SPEC[TC_P2_CANDS] = {{0, 192, 0}, {1, 48, 0}, {1, 192, 0}, {1, 192, 1}, {1, 768, 0}};
 
-// One phase-2 schedule of every network's upper-triangle P and C tiles.
+// One phase-2 schedule of every network's upper-triangle P and C tiles.  A P
+// tile is one unit of the LPT assignment (its whole K) and is listed as its
+// K chunks, consecutively, on the pair it is assigned to (see P2Item).
 void build_p2(const std::vector<const Dev *> &ds, int pairs, const P2Spec &sp, std::vector<int> &off,
               std::vector<int> &tiles, std::vector<int> &nets)
 {
@@ -1653,13 +1740,22 @@ void build_p2(const std::vector<const Dev *> &ds, int pairs, const P2Spec &sp, s
                     all.push_back({c, {(int)((isP ? 0x80000000u : 0u) | ((uint32_t)bm << 16) | (uint32_t)bn), k}});
         }
     }
-    std::vector<std::pair<int, int>> out;
-    lpt_lists(all, std::min<int>(pairs, (int)all.size()), sp.interleave != 0, off, out);
+    std::vector<int> uoff;
+    std::vector<std::pair<int, int>> units;
+    lpt_lists(all, std::min<int>(pairs, (int)all.size()), sp.interleave != 0, uoff, units);
+    off.assign(1, 0);
     tiles.clear();
     nets.clear();
-    for (auto &t : out) {
-        tiles.push_back(t.first);
-        nets.push_back(t.second);
+    for (size_t p = 0; p + 1 < uoff.size(); ++p) {
+        for (int q = uoff[p]; q < uoff[p + 1]; ++q) {
+            const int code = units[q].first, net = units[q].second;
+            const int nch = code < 0 ? p2_chunks(*ds[net]) : 1;
+            for (int c = 0; c < nch; ++c) {
+                tiles.push_back(code | (c << 24));
+                nets.push_back(net);
+            }
+        }
+        off.push_back((int)tiles.size());
     }
 }
 

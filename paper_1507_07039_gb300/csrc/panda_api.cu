@@ -178,7 +178,12 @@ int plan_memory(panda_ctx *c)
         }
         DALLOC(d.Ph, Tp * Tp);
         DALLOC(d.Pl, Tp * Tp);
-        DALLOC(d.p1_acc, (Tp / 256) * (Gp / 256) * 2 * (size_t)128 * 256);  // phase 1: per CTA
+        // running sums of the long products' K chunks: one 128 x 256 slot per CTA of phase 1's
+        // grid, and at least one per CTA of the persistent phase 2 (at most one per SM)
+        int nsm = 0;
+        CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
+        const size_t slots = std::max<size_t>((Tp / 256) * (Gp / 256) * 2, (size_t)nsm);
+        DALLOC(d.p1_acc, slots * 128 * 256);
         if (d.fp8) {  // W.C and W^T.W on E4M3 copies; no BF16 copy of C
             for (int b = 0; b < 2; ++b) {
                 DALLOC(d.W8[b], Tp * Gp);
