@@ -525,8 +525,13 @@ constexpr int EPI1 = 8, THREADS1 = 64 + 32 * EPI1;
 // alternate between chunks, the epilogue warps (idle during the main loop)
 // add each finished chunk into a running FP32 sum in global memory (this
 // CTA's own 128 x 256 slot, L2-resident), and R-num, which is short, runs
-// last in the buffer the chunks leave free.
-constexpr int P1_CHUNK = 16;
+// last in the buffer the chunks leave free.  32 k-blocks (2048 genes) per
+// chunk: 16 halved the drift again but cost phase 1 5% more time (the
+// drains' L2 traffic), 32 costs 4%.
+constexpr int P1_CHUNK = 32;
+// Phase 2's P tiles (K over genes, a few percent of its work) likewise, in
+// chunks of P2_CHUNK k-blocks.
+constexpr int P2_CHUNK = 64;
 
 // v added into a running-sum entry in L2 without a round trip (the entry's
 // earlier chunks were written by this same thread, so the adds of one entry
@@ -985,7 +990,7 @@ struct P2Cfg {
 // A scheduled phase-2 item.  A C tile (bit 31 clear: bits 16-30 row block,
 // 0-15 column block) is one item over all of its K (TFs).  A P tile's K runs
 // over all genes, so, like phase 1's availability product, it is summed in
-// chunks of P1_CHUNK k-blocks, each into a fresh accumulator: the tile is
+// chunks of P2_CHUNK k-blocks, each into a fresh accumulator: the tile is
 // scheduled as consecutive items on one CTA pair (bit 31 set: bits 24-30 the
 // chunk, 16-23 row block, 0-15 column block); the epilogue adds every chunk
 // but the last into the CTA's running-sum slot and finishes the tile on the
@@ -994,7 +999,7 @@ struct P2Item {
     bool isP;
     int bm, bn, kb0, kb1, chunk, nchunks;
 };
-__host__ __device__ inline int p2_chunks(const Dev &d) { return (d.Gp / BK + P1_CHUNK - 1) / P1_CHUNK; }
+__host__ __device__ inline int p2_chunks(const Dev &d) { return (d.Gp / BK + P2_CHUNK - 1) / P2_CHUNK; }
 __device__ __forceinline__ P2Item p2_item(int tile, const Dev &d)
 {
     P2Item it;
@@ -1004,8 +1009,8 @@ __device__ __forceinline__ P2Item p2_item(int tile, const Dev &d)
         it.bm = (tile >> 16) & 0xff;
         it.chunk = (tile >> 24) & 0x7f;
         it.nchunks = p2_chunks(d);
-        it.kb0 = it.chunk * P1_CHUNK;
-        it.kb1 = min(d.Gp / BK, it.kb0 + P1_CHUNK);
+        it.kb0 = it.chunk * P2_CHUNK;
+        it.kb1 = min(d.Gp / BK, it.kb0 + P2_CHUNK);
     } else {
         it.bm = (tile >> 16) & 0x7fff;
         it.chunk = 0;
