@@ -243,6 +243,29 @@ __device__ __forceinline__ void ld_rows4_split(const __nv_bfloat16 *h, const __n
     }
 }
 
+// For a matrix held as a BF16 split pair: 8 consecutive values hi + lo of
+// rows p and p + 16 ld (16-byte loads of each half), into v[0..1] and v[2..3]
+__device__ __forceinline__ void ld_rows2x8_split(const __nv_bfloat16 *h, const __nv_bfloat16 *l, int ld,
+                                                 float4 (&v)[4])
+{
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const size_t o = (size_t)(16 * i) * ld;
+        const uint4 a = *reinterpret_cast<const uint4 *>(h + o), b = *reinterpret_cast<const uint4 *>(l + o);
+        const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+        float f[8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 x = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&av[q]));
+            const float2 y = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&bv[q]));
+            f[2 * q] = x.x + y.x;
+            f[2 * q + 1] = x.y + y.y;
+        }
+        v[2 * i] = make_float4(f[0], f[1], f[2], f[3]);
+        v[2 * i + 1] = make_float4(f[4], f[5], f[6], f[7]);
+    }
+}
+
 // 16 BF16 values held as 8 packed pairs: two 16-byte stores, or the masked entries
 __device__ __forceinline__ void st16_packed(__nv_bfloat16 *dst, const uint32_t (&p)[8], uint32_t mask)
 {
@@ -1304,13 +1327,15 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
             const float nk_ = krow ? nrm[k] : 0.0f;
             // old values, loaded coalesced (8 rows x 64 B per load): lane l takes columns
             // 4 (l & 3) .. + 3 of the warp's rows (l >> 2) + 8 i, i = 0..3 (rows past the network
-            // are padding inside the array; their values are never used)
-            const size_t xo = (size_t)(k0 + (lane >> 2)) * ld + n0 + 4 * (lane & 3);
+            // are padding inside the array; their values are never used).  A split-held C: lane l
+            // takes columns 8 (l & 1) .. + 7 of rows (l >> 1) + 16 i, i = 0..1, 16 bytes of each half
+            const size_t xo = sst ? (size_t)(k0 + (lane >> 1)) * ld + n0 + 8 * (lane & 1)
+                                  : (size_t)(k0 + (lane >> 2)) * ld + n0 + 4 * (lane & 3);
             const float *xblk = sst ? nullptr : X + xo;
             float4 nxt[4];
             if (n0 + c_begin * 16 < ld) {
                 if (sst)
-                    ld_rows4_split(Xh + xo + c_begin * 16, Xl + xo + c_begin * 16, ld, nxt);
+                    ld_rows2x8_split(Xh + xo + c_begin * 16, Xl + xo + c_begin * 16, ld, nxt);
                 else
                     ld_rows4(xblk + c_begin * 16, ld, nxt);
             }
@@ -1334,7 +1359,8 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 // old values to this lane's own row through the staging block
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    float *b = blk + ((lane >> 2) + 8 * i) * 17 + 4 * (lane & 3);
+                    float *b = sst ? blk + ((lane >> 1) + 16 * (i >> 1)) * 17 + 8 * (lane & 1) + 4 * (i & 1)
+                                   : blk + ((lane >> 2) + 8 * i) * 17 + 4 * (lane & 3);
                     b[0] = nxt[i].x; b[1] = nxt[i].y; b[2] = nxt[i].z; b[3] = nxt[i].w;
                 }
                 __syncwarp();
@@ -1344,7 +1370,7 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 __syncwarp();  // the block takes the new values next
                 if (c + 1 < c_end && j0 + 16 < ld) {  // next sub-chunk's old values, in flight meanwhile
                     if (sst)
-                        ld_rows4_split(Xh + xo + (c + 1) * 16, Xl + xo + (c + 1) * 16, ld, nxt);
+                        ld_rows2x8_split(Xh + xo + (c + 1) * 16, Xl + xo + (c + 1) * 16, ld, nxt);
                     else
                         ld_rows4(xblk + (c + 1) * 16, ld, nxt);
                 }
@@ -1425,9 +1451,36 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 for (int q = 0; q < 16; ++q)
                     blk[lane * 17 + q] = (vmask >> q & 1u) ? old[q] : 0.0f;
                 __syncwarp();
-                // (a) row-major copies, coalesced: lane l takes 4 columns of rows (l >> 2) + 8 i
+                // (a) row-major copies, coalesced.  A split-held C: lane l takes 8 columns of rows
+                // (l >> 1) + 16 i, 16-byte stores of each half
+                if (sst) {
 #pragma unroll
-                for (int i2 = 0; i2 < 4; ++i2) {
+                    for (int i2 = 0; i2 < 2; ++i2) {
+                        const int rr = (lane >> 1) + 16 * i2, kk = k0 + rr, jj = j0 + 8 * (lane & 1);
+                        float f[8];
+#pragma unroll
+                        for (int q = 0; q < 8; ++q)
+                            f[q] = blk[rr * 17 + 8 * (lane & 1) + q];
+                        uint32_t h4[4], l4[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            split_pair(f[2 * q], f[2 * q + 1], h4[q], l4[q]);
+                        const size_t ro = (size_t)kk * ld + jj;
+                        if (kk < jj && jj + 7 < nn) {
+                            *reinterpret_cast<uint4 *>(Xh + ro) = make_uint4(h4[0], h4[1], h4[2], h4[3]);
+                            *reinterpret_cast<uint4 *>(Xl + ro) = make_uint4(l4[0], l4[1], l4[2], l4[3]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 8; ++q)
+                                if (kk < jj + q && jj + q < nn) {
+                                    reinterpret_cast<uint16_t *>(Xh)[ro + q] = (uint16_t)(h4[q >> 1] >> (16 * (q & 1)));
+                                    reinterpret_cast<uint16_t *>(Xl)[ro + q] = (uint16_t)(l4[q >> 1] >> (16 * (q & 1)));
+                                }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int i2 = 0; i2 < (sst ? 0 : 4); ++i2) {
                     const int rr = (lane >> 2) + 8 * i2, kk = k0 + rr, jj = j0 + 4 * (lane & 3);
                     float f[4];
 #pragma unroll
