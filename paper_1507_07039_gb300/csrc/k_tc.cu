@@ -948,7 +948,9 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
 }
 
 
-// One network: a grid of 2 x (Tp / 256) by Gp / 256 CTAs, one pair per tile.
+// One network: persistent CTA pairs (at most one per SM pair); pair p takes
+// the tiles p, p + pairs, p + 2 pairs, ... of the gene-block-major order
+// (the TF tiles of a gene block run side by side and share its C rows in L2).
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
     k_tc_phase1(const __grid_constant__ TcMaps maps, const __grid_constant__ Dev d, int cur)
 {
@@ -956,8 +958,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
         return;
     phase1_tmem_alloc();
     int g = 0, tile = 0, u[2] = {0, 0};
-    float *scr = d.p1_acc + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * P1_SLOT;
-    phase1_tile(maps, d, cur, blockIdx.x >> 1, blockIdx.y, g, tile, u, scr);
+    float *scr = d.p1_acc + (size_t)blockIdx.x * P1_SLOT;
+    const int nmt = d.Tp / 256, ntiles = nmt * (d.Gp / 256), pairs = gridDim.x >> 1;
+    for (int q = blockIdx.x >> 1; q < ntiles; q += pairs)
+        phase1_tile(maps, d, cur, q % nmt, q / nmt, g, tile, u, scr);
     phase1_tmem_free();
 }
 
@@ -1706,8 +1710,8 @@ constexpr size_t pair_smem() { return 1024 + (size_t)PAIR_ST * PAIR_STAGE + size
 struct TcHost {
     TcMaps maps;
     int *sched_off = nullptr;  // [grid2 + 1] offsets into sched
-    int *sched = nullptr;      // packed tiles: bit 31 = P, bits 16-30 = row block, bits 0-15 = column block
-    int grid2 = 0;
+    int *sched = nullptr;      // packed phase-2 items (see P2Item)
+    int grid1 = 0, grid2 = 0;  // CTAs of the persistent phase-1 and phase-2 launches
 };
 
 // Cost of a phase-2 tile in MMA issue slots (a BF16 MMA of K = 16 and an E4M3
@@ -1931,6 +1935,7 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales)
         std::vector<int> off, tiles;
         build_schedule(d, nsm / 2, off, tiles);  // one list per CTA pair
         h->grid2 = 2 * ((int)off.size() - 1);
+        h->grid1 = 2 * std::min(nsm / 2, (d.Tp / 256) * (d.Gp / 256));
         if ((e = cudaMalloc(&h->sched_off, off.size() * sizeof(int))) ||
             (e = cudaMalloc(&h->sched, tiles.size() * sizeof(int))) ||
             (e = cudaMemcpy(h->sched_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
@@ -1956,8 +1961,7 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
     const TcHost &h = *static_cast<const TcHost *>(d.tc_host);
     const TcMaps &m = h.maps;
     ke.mark(s);
-    dim3 g1(2 * (d.Tp / 256), d.Gp / 256);
-    k_tc_phase1<<<g1, THREADS1, phase1_smem(), s>>>(m, d, cur);
+    k_tc_phase1<<<h.grid1, THREADS1, phase1_smem(), s>>>(m, d, cur);
     ke.mark(s);
     cudaError_t e = launch_reduce_wnorms(d, s);
     if (e)

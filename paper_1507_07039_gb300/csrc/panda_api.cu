@@ -178,12 +178,11 @@ int plan_memory(panda_ctx *c)
         }
         DALLOC(d.Ph, Tp * Tp);
         DALLOC(d.Pl, Tp * Tp);
-        // running sums of the long products' K chunks: one 128 x 256 slot per CTA of phase 1's
-        // grid, and at least one per CTA of the persistent phase 2 (at most one per SM)
+        // running sums of the long products' K chunks: one 128 x 256 slot per CTA of the
+        // persistent phase-1 and phase-2 launches (at most one CTA per SM)
         int nsm = 0;
         CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
-        const size_t slots = std::max<size_t>((Tp / 256) * (Gp / 256) * 2, (size_t)nsm);
-        DALLOC(d.p1_acc, slots * 128 * 256);
+        DALLOC(d.p1_acc, (size_t)nsm * 128 * 256);
         if (d.fp8) {  // W.C and W^T.W on E4M3 copies; no BF16 copy of C
             for (int b = 0; b < 2; ++b) {
                 DALLOC(d.W8[b], Tp * Gp);

@@ -359,11 +359,10 @@ def test_device_bytes_follow_the_memory_plan(panda, monkeypatch):
     Tp, Gp = -(-T // 256) * 256, -(-G // 256) * 256
     assert got[1] >= 4 * (4 * Tp * Gp + Tp * Tp) + 2 * 2 * Gp * Gp
     # no FP32 C held: less than an FP32 C's 4 Gp^2 on top of the plan, whose largest other item is
-    # the running-sum slots of the long products (128 x 256 floats per CTA of phase 1, at least
-    # one per SM)
+    # the running-sum slots of the long products (128 x 256 floats per SM)
     import torch
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    slots = max((Tp // 256) * (Gp // 256) * 2, nsm) * 128 * 256 * 4
+    slots = nsm * 128 * 256 * 4
     assert got[1] < 4 * (4 * Tp * Gp + Tp * Tp) + 2 * 2 * Gp * Gp + slots + 4 * Gp * Gp
     assert got[2] == got[1]
     assert peak[1] == got[1] + 4 * Gp * Gp
