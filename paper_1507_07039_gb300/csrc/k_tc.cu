@@ -837,6 +837,13 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
             if (lane == 0)  // this warp is done with the buffer: tell the even CTA's MMA issuer
                 mbar_arrive_cluster(bfree_even + (uint32_t)b * (uint32_t)sizeof(uint64_t));
         }
+        // the running sum's first sub-chunk, from L2 (where the adds landed), in flight while the
+        // last chunk and R-num finish; each later one is fetched a sub-chunk ahead
+        const float *srow = scr + (size_t)(half * 128) * 128 + r;
+        float snxt[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q)
+            snxt[q] = (live && nc > 1) ? __ldcg(srow + (size_t)q * 128) : 0.0f;
         live = live && wait_bounded(&sy.accum, tpar, &sy.abort, ctl) && !*(volatile int *)&sy.abort;
         tc_fence_after();
         const float a = ctl->alpha, keep = 1.0f - a, halfa = 0.5f * a;
@@ -844,18 +851,26 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
 #pragma unroll 1
         for (int c = 0; c < 8 && live; ++c) {
             const int cc = half * 128 + c * 16, j0 = n0 + cc;
-            float w[16], rr[16], aa[16], wn[16];
+            float w[16], rr[16], aa[16], wn[16], sa[16];
 #pragma unroll
-            for (int q = 0; q < 16; ++q)
+            for (int q = 0; q < 16; ++q) {
                 w[q] = nxt[q];
-            if (c < 7)
-                ld16(wrow + (c + 1) * 16, nxt);  // next sub-chunk's W, in flight meanwhile
+                sa[q] = snxt[q];
+            }
+            if (c < 7) {
+                ld16(wrow + (c + 1) * 16, nxt);  // next sub-chunk's W and running sum, in flight meanwhile
+                if (nc > 1) {
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        snxt[q] = __ldcg(srow + (size_t)((c + 1) * 16 + q) * 128);
+                }
+            }
             tmem_ld16(trow + (uint32_t)bR * 256u + cc, rr);
             tmem_ld16(trow + (uint32_t)(bR ^ 1) * 256u + cc, aa);  // the last A-num chunk
             if (nc > 1) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q)
-                    aa[q] = __ldcg(scr + (size_t)(cc + q) * 128 + r) + aa[q];  // L2: where the adds landed
+                    aa[q] = sa[q] + aa[q];
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
