@@ -150,3 +150,30 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable():
     B = np.full((128, 64), 2.0, np.float32)
     D = panda.panda_selftest_tc_gemm(A, B, terms=1)
     assert np.all(D == 128.0)
+
+
+@pytest.mark.parametrize("K", [1024, 4096, 17152])
+def test_accumulation_drift_of_a_long_mma_chain(K):
+    """Sums of positive products on the pair pipeline (three-term split, one
+    accumulator over all of K) drift toward zero as K grows, while signed
+    sums do not: the MMA's FP32 accumulation drops low bits on every step.
+    Bound: each of the 3 K / 16 accumulating MMAs loses at most one unit of
+    the running sum's last place, |error| <= (3 K / 16) 2^-23 sum |a||b|.
+    (This is why the library sums its products over all genes in chunks.)"""
+    from paper_1507_07039_gb300 import panda
+    rng = np.random.default_rng(K)
+    out = {}
+    for kind in ("positive", "signed"):
+        A = rng.random((256, K)).astype(np.float32)
+        B = rng.random((256, K)).astype(np.float32)
+        if kind == "signed":
+            A -= 0.5
+            B -= 0.5
+        D = panda.panda_selftest_tc_gemm(A, B, terms=13)
+        A64, B64 = A.astype(np.float64), B.astype(np.float64)
+        rel = (D - A64 @ B64.T) / (np.abs(A64) @ np.abs(B64).T)
+        out[kind] = (float(np.abs(rel).max()), float(rel.mean()))
+        assert np.abs(rel).max() <= 3 * K / 16 * 2.0 ** -23, (kind, out[kind])
+    print(f"\nK={K}: positive max {out['positive'][0]:.2e} mean {out['positive'][1]:+.2e}; "
+          f"signed max {out['signed'][0]:.2e} mean {out['signed'][1]:+.2e}")
+    assert out["positive"][1] < 0  # toward zero

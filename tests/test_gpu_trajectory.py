@@ -97,3 +97,24 @@ def test_human_sized_trajectory_to_convergence(t1000_full, prec):
     inputs, o = t1000_full
     assert o["converged"]
     _check(inputs, o, prec, "1000 x 17000 to convergence", FULL_RUN_TOL[prec])
+
+
+def test_bf16x3_tracks_fp32_along_the_human_sized_run():
+    """BF16X3 against the FP32 path, both on the device, along the 50
+    iterations of the human-sized run (no oracle: seconds).  Regression bounds
+    of the chunked sums (one accumulator per product deviated 9.5e-5 at t = 3
+    and 6.5e-2 at t = 50)."""
+    from paper_1507_07039_gb300 import panda
+    W0, P0, C0 = gh.inputs("human1000x17000")
+    steps = (1, 3, 10, 20, 30, 50)
+    got = {}
+    for prec in (0, 1):
+        with panda.PandaContext(W0, P0, C0, prec=prec) as ctx:
+            done, got[prec] = 0, []
+            for t in steps:
+                ctx.run(0.1, 0.0, t - done)
+                done = t
+                got[prec].append(ctx.get(want=(True, False, False))[0])
+    dev = [float(np.max(np.abs(a.astype(np.float64) - b))) for a, b in zip(got[1], got[0])]
+    print("\nmax |W_bf16x3 - W_fp32| at t = " + ", ".join(f"{t}: {d:.2e}" for t, d in zip(steps, dev)))
+    assert dev[1] <= 5e-5 and dev[-1] <= 2e-2, dev
