@@ -83,4 +83,5 @@ def test_large_network_gene_subsample(large_subnetwork, prec):
     orc.set_threads(os.cpu_count() or 1)
     o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 4)
     g = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 4)
-    gh.assert_parity(g, o, prec, "1600 x 2000 subsample")
+    e = gh.assert_parity(g, o, prec, "1600 x 2000 subsample")
+    print(f"\n1600 x 2000 subsample prec {prec}, 4 iterations: " + ", ".join(f"{k} {v:.3e}" for k, v in e.items()))
