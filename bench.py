@@ -476,8 +476,9 @@ def time_gpu(panda, torch, W0, P0, C0, prec, steps, warmup, world, local_rank, w
     ck = clocks.stop() if clocks else None
     barrier(world)
     kstats = [(name, a[0], a[1]) for name, a in acc.items()]
+    layout = panda.panda_phase1_layout(ctx.h) if prec != panda.PANDA_FP32 else None
     ctx.close()
-    return ms, kstats, ck
+    return ms, kstats, ck, layout
 
 
 def run_segments(panda, torch, ctx, steps, T, G, device) -> float:
@@ -553,20 +554,20 @@ def run_ours(args, wl, rank, world, local_rank):
     W0, P0, C0 = synth.make_inputs(wl)
     T, G = wl.T, wl.G
 
-    ms, kstats, ck = time_gpu(panda, torch, W0, P0, C0, prec, args.steps, args.warmup, world,
-                              local_rank, rank == 0)
+    ms, kstats, ck, layout = time_gpu(panda, torch, W0, P0, C0, prec, args.steps, args.warmup, world,
+                                      local_rank, rank == 0)
     ms_max = max_over_ranks(ms, world, torch.device("cuda", local_rank))
     value = world * args.steps / (ms_max / 1000.0)
 
     # the other precision on the same GPU, for the BF16-split vs FP32 comparison
     other = None
     if args.compare and prec != panda.PANDA_FP32:
-        ms32, _, _ = time_gpu(panda, torch, W0, P0, C0, panda.PANDA_FP32, max(5, args.steps // 4),
+        ms32, _, _, _ = time_gpu(panda, torch, W0, P0, C0, panda.PANDA_FP32, max(5, args.steps // 4),
                               args.warmup, world, local_rank, False)
         other = {"fp32_iters_per_s": world * max(5, args.steps // 4) / (max_over_ranks(ms32, world, torch.device("cuda", local_rank)) / 1000.0)}
         if prec == panda.PANDA_BF16X3:  # the lower-precision modes beside it (their errors: tests, notes)
             for name, code in (("bf16x2", panda.PANDA_BF16X2), ("fp8mix", panda.PANDA_FP8MIX)):
-                ms2, _, _ = time_gpu(panda, torch, W0, P0, C0, code, max(5, args.steps // 2),
+                ms2, _, _, _ = time_gpu(panda, torch, W0, P0, C0, code, max(5, args.steps // 2),
                                      args.warmup, world, local_rank, False)
                 other[name + "_iters_per_s"] = world * max(5, args.steps // 2) / (
                     max_over_ranks(ms2, world, torch.device("cuda", local_rank)) / 1000.0)
@@ -633,6 +634,7 @@ def run_ours(args, wl, rank, world, local_rank):
                        "precision": args.prec, "step": "one message-passing iteration (Eqs. 2-7)",
                        "l2": "no flush: inputs larger than L2 (C alone is %.2f GB)" % (4.0 * G * G / 1e9),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
+            "phase1_launch": layout,
             "useful_tflops": value / world * algorithmic_flops(T, G) / 1e12,
             "roofline": roof,
             "cpu_baseline": cpu,

@@ -299,6 +299,33 @@ int panda_batch_schedule(const panda_batch *b, int *p1, int *p2, float *p1_ms, i
  * (phase = 2); NULL past the last candidate. */
 const char *panda_batch_schedule_name(int phase, int k);
 
+/* How phase 1 of one network of T TFs and G genes would be spread over
+ * `pairs` persistent CTA pairs in tensor-core mode prec (a host computation:
+ * no device is needed).  Phase 1 computes the W' tiles of Eqs. 2-3 and 7;
+ * each 256 x 256 tile sums the availability numerator W.C over all genes in
+ * chunks of 32 k-blocks (64 genes each; 128 under PANDA_FP8MIX), then the
+ * responsibility numerator and the epilogue.  Whole tiles run in rounds;
+ * when the tile count is not a multiple of pairs, the tiles of the last two
+ * rounds are cut at chunk boundaries into equal shares of MMA work.  A cut
+ * tile's head (chunks 0 .. b - 1) runs first on its pair, its tail (chunks
+ * b .. n - 1, the responsibility numerator, the epilogue) last on another,
+ * which waits for the head: all_resident = 0 (not every pair known to be
+ * resident at once) makes no cuts.  Up to cap pieces are written to pieces,
+ * six ints each, in the order each pair runs them, pair by pair: pair, TF
+ * block mt, gene block nt, first chunk c0, end chunk c1 (c1 = n for a piece
+ * that ends the tile), cut index (-1 for a whole tile).  *n_pieces receives
+ * the total count.  Returns the number of cut tiles, or PANDA_EINVAL (T or G
+ * < 1, prec not a tensor-core mode, pairs < 1, n_pieces NULL, or pieces NULL
+ * with cap > 0). */
+int panda_phase1_plan(int T, int G, int prec, int pairs, int all_resident, int *pieces, int cap, int *n_pieces);
+
+/* The phase-1 launch a tensor-core context uses (see panda_phase1_plan):
+ * *pairs its persistent CTA pairs, *clusters the two-CTA clusters the
+ * device holds at once for that kernel (cuts are made only when every pair
+ * is resident), *cuts the tiles cut between two pairs; any pointer may be
+ * NULL.  Returns 0, or PANDA_EINVAL for NULL c or an FP32 context. */
+int panda_phase1_layout(const panda_ctx *c, int *pairs, int *clusters, int *cuts);
+
 const char *panda_batch_last_error(const panda_batch *b);
 void panda_batch_destroy(panda_batch *b);
 

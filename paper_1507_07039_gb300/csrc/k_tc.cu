@@ -565,6 +565,38 @@ __device__ __forceinline__ void red_add(float *p, float v)
 }
 constexpr size_t P1_SLOT = 128 * 256;  // floats of one CTA's running-sum slot
 
+// A tile cut between two CTA pairs at a chunk boundary: the pair holding its
+// head (chunks 0 .. b - 1) adds them into a running-sum slot of its own for
+// that tile and raises one flag per CTA rank once every add has landed; the
+// pair holding its tail (chunks b .. , R-num, the epilogue) waits for the flag
+// of its rank before its first access to the slot, so each entry's chunks are
+// still added in chunk order.  Gives up like wait_bounded.
+__device__ __forceinline__ void flag_raise(int *f)
+{
+    __threadfence();  // the adds of every epilogue thread of this CTA (ordered before by a barrier)
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(f), "r"(1) : "memory");
+}
+__device__ __forceinline__ bool flag_wait_bounded(int *f, int *abort, Ctl *ctl)
+{
+    const long long t0 = clock64();
+    while (true) {
+        int v;
+        asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+        if (v) {
+            *f = 0;  // consumed: the next launch's head raises it again
+            return true;
+        }
+        if (*(volatile int *)abort)
+            return false;
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+            atomicExch(abort, 1);
+            atomicOr(&ctl->status, ST_TIMEOUT);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
+
 struct Sync1 {
     uint64_t full[ST1], empty[ST1];
     uint64_t accum;
@@ -629,16 +661,20 @@ __device__ __forceinline__ void phase1_tmem_free()
     }
 }
 
-// The body of phase 1 for the tile (mt, nt) of one network: maps and d are
-// that network's (kernel parameters for one network, entries of arrays in
-// global memory for a set), cur its current W buffer, scr this CTA's slot of
-// 128 x 256 floats for the running A-num sum ([column][row]).  g counts the
-// pipeline stages, tile the tiles and u[b] the drains of TMEM buffer b this CTA
-// has run before (barrier phases follow them); all advance here.  Both CTAs of
+// The body of phase 1 for the A-num chunks c0 .. c1 - 1 of the tile (mt, nt)
+// of one network (c1 at or past the chunk count: through the last chunk, then
+// R-num and the epilogue): maps and d are that network's (kernel parameters
+// for one network, entries of arrays in global memory for a set), cur its
+// current W buffer, scr this CTA's slot of 128 x 256 floats for the running
+// A-num sum ([column][row]).  A piece that does not start at chunk 0 waits for
+// *flag before it touches scr; one that does not end the tile raises *flag
+// when its adds have landed (flag NULL: a whole tile).  g counts the pipeline
+// stages, tile the pieces and u[b] the drains of TMEM buffer b this CTA has
+// run before (barrier phases follow them); all advance here.  Both CTAs of
 // the pair run every call together and end it at a cluster barrier, after
-// which TMEM is free for the next tile.
-__device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, int cur, int mt, int nt, int &g,
-                                            int &tile, int (&u)[2], float *scr)
+// which TMEM is free for the next piece.
+__device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, int cur, int mt, int nt, int c0,
+                                            int c1, int *flag, int &g, int &tile, int (&u)[2], float *scr)
 {
     Ctl *ctl = d.ctl;
     if (!ctl->active)  // both CTAs of a pair see the same value and leave together
@@ -657,19 +693,27 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
     const int m0 = mt * 256 + 128 * (int)rank;  // this CTA's 128 rows (TFs)
     const int n0 = nt * 256;                    // the tile's 256 columns (genes)
     // k-blocks kb: R-num over TFs (kb < nR, 64 BF16 per row) and A-num over genes (kb >= nR, 64 BF16,
-    // or 128 E4M3 under FP8MIX).  They are issued in the order s = 0 .. nk - 1: first A-num in nc
-    // chunks of P1_CHUNK k-blocks (chunk c in TMEM buffer c & 1), then R-num (buffer nc & 1).
-    const int nR = d.Tp / BK, nA = d.Gp / (d.fp8 ? 2 * BK : BK), nk = nR + nA;
+    // or 128 E4M3 under FP8MIX).  A-num runs in nc chunks of P1_CHUNK k-blocks (chunk c in TMEM
+    // buffer c & 1), R-num after the last chunk (buffer nc & 1).  This piece issues, in the order
+    // s = 0 .. nk - 1, the k-blocks of chunks c0 .. c1 - 1 and, if it ends the tile, R-num.
+    const int nR = d.Tp / BK, nA = d.Gp / (d.fp8 ? 2 * BK : BK);
     const int nc = (nA + P1_CHUNK - 1) / P1_CHUNK, bR = nc & 1;
-    auto kb_of = [nR, nA](int s) { return s < nA ? nR + s : s - nA; };
+    c1 = c1 < nc ? c1 : nc;
+    const bool ends = c1 == nc;                              // R-num and the epilogue are this piece's
+    const int a0 = c0 * P1_CHUNK, nAp = min(c1 * P1_CHUNK, nA) - a0;  // the piece's A-num k-blocks
+    const int nk = nAp + (ends ? nR : 0);
+    auto kb_of = [nR, a0, nAp](int s) { return s < nAp ? nR + a0 + s : s - nAp; };
+    const int cd = c1 < nc - 1 ? c1 : nc - 1;  // chunks c0 .. cd - 1 are drained into scr
 
-    const int g0 = g;      // stages run by this CTA before this tile
-    const uint32_t tpar = (uint32_t)tile & 1u;  // phase of the accumulator barrier for this tile
-    const int u0[2] = {u[0], u[1]};  // drains of each buffer before this tile
+    const int g0 = g;      // stages run by this CTA before this piece
+    const uint32_t tpar = (uint32_t)tile & 1u;  // phase of the accumulator barrier for this piece
+    const int u0[2] = {u[0], u[1]};  // drains of each buffer before this piece
     g += nk;
     ++tile;
-    u[0] += nc / 2;        // chunks 0, 2, .. < nc - 1 are drained from buffer 0
-    u[1] += (nc - 1) / 2;  // chunks 1, 3, .. < nc - 1 from buffer 1
+    if (cd > c0) {  // the piece's i-th drain of a buffer is chunk c0 + 2 i or c0 + 1 + 2 i
+        u[c0 & 1] += (cd - c0 + 1) / 2;
+        u[(c0 & 1) ^ 1] += (cd - c0) / 2;
+    }
     if (threadIdx.x == 0) {
         sy.issued = 0;
         sy.consumed = 0;
@@ -733,9 +777,10 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                 const int a = kb - nR, c = a / P1_CHUNK;
                 const int buf = kb >= nR ? (c & 1) : bR;
                 const bool fresh = kb >= nR ? a % P1_CHUNK == 0 : kb == 0;
-                const int prev = kb >= nR ? c - 2 : nc - 2;  // chunk that last used buf (< 0: none)
-                if (fresh && prev >= 0 &&
-                    !wait_bounded(&sy.buf_free[buf], (uint32_t)(u0[buf] + (prev >> 1)) & 1u, &sy.abort, ctl))
+                const int prev = kb >= nR ? c - 2 : nc - 2;  // chunk that last used buf (< c0: none here)
+                if (fresh && prev >= c0 &&
+                    !wait_bounded(&sy.buf_free[buf], (uint32_t)(u0[buf] + ((prev - c0) >> 1)) & 1u, &sy.abort,
+                                  ctl))
                     break;
                 if (!wait_bounded(&sy.full[st], (uint32_t)((g0 + s) / ST1) & 1u, &sy.abort, ctl))
                     break;
@@ -809,10 +854,16 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
         // while the MMAs run on: add each finished A-num chunk but the last into the running sum
         // (this thread's row r, its 128 columns; [column][row] so a warp's accesses are contiguous)
         bool live = true;
+        if (c0 > 0) {  // the tile's head was added into scr by another pair: wait for its flag
+            if (threadIdx.x == 64 && !flag_wait_bounded(flag, &sy.abort, ctl))
+                sy.abort = 1;
+            epi_bar2();
+            live = !*(volatile int *)&sy.abort;
+        }
         const uint32_t bfree_even = mapa_shared(smem_u32(&sy.buf_free[0]), 0);
-        for (int c = 0; c + 1 < nc && live; ++c) {
+        for (int c = c0; c < cd && live; ++c) {
             const int b = c & 1;
-            live = wait_bounded(&sy.chunk_done[b], (uint32_t)(u0[b] + (c >> 1)) & 1u, &sy.abort, ctl) &&
+            live = wait_bounded(&sy.chunk_done[b], (uint32_t)(u0[b] + ((c - c0) >> 1)) & 1u, &sy.abort, ctl) &&
                    !*(volatile int *)&sy.abort;
             tc_fence_after();
             if (!live)
@@ -837,6 +888,12 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
             if (lane == 0)  // this warp is done with the buffer: tell the even CTA's MMA issuer
                 mbar_arrive_cluster(bfree_even + (uint32_t)b * (uint32_t)sizeof(uint64_t));
         }
+        if (!ends) {  // a head piece: its adds are done; the accumulator barrier's phase still completes
+            live = live && wait_bounded(&sy.accum, tpar, &sy.abort, ctl) && !*(volatile int *)&sy.abort;
+            epi_bar2();
+            if (threadIdx.x == 64 && live)
+                flag_raise(flag);
+        } else {
         // the running sum's first sub-chunk, from L2 (where the adds landed), in flight while the
         // last chunk and R-num finish; each later one is fetched a sub-chunk ahead
         const float *srow = scr + (size_t)(half * 128) * 128 + r;
@@ -953,6 +1010,7 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
                 d.hpart[(size_t)nt * d.nbT + slot] = hs;
             }
         }
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -963,20 +1021,27 @@ __device__ __forceinline__ void phase1_tile(const TcMaps &maps, const Dev &d, in
 }
 
 
-// One network: persistent CTA pairs (at most one per SM pair); pair p takes
-// the tiles p, p + pairs, p + 2 pairs, ... of the gene-block-major order
-// (the TF tiles of a gene block run side by side and share its C rows in L2).
+// One network: persistent CTA pairs (at most one per SM pair), pair p over
+// its host-built list items[off[p] .. off[p + 1]) of pieces (mt, nt, chunks
+// c0 | c1 << 16, cut): whole tiles (cut < 0) in rounds of the gene-block-major
+// order, and tiles cut between two pairs at a chunk boundary, whose two
+// pieces meet in running-sum slot `cut` (see build_p1).
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1)
-    k_tc_phase1(const __grid_constant__ TcMaps maps, const __grid_constant__ Dev d, int cur)
+    k_tc_phase1(const __grid_constant__ TcMaps maps, const __grid_constant__ Dev d, int cur, const int4 *items,
+                const int *off)
 {
     if (!d.ctl->active)  // both CTAs of a pair see the same value and leave together
         return;
     phase1_tmem_alloc();
     int g = 0, tile = 0, u[2] = {0, 0};
-    float *scr = d.p1_acc + (size_t)blockIdx.x * P1_SLOT;
-    const int nmt = d.Tp / 256, ntiles = nmt * (d.Gp / 256), pairs = gridDim.x >> 1;
-    for (int q = blockIdx.x >> 1; q < ntiles; q += pairs)
-        phase1_tile(maps, d, cur, q % nmt, q / nmt, g, tile, u, scr);
+    const int pair = blockIdx.x >> 1, rank = (int)cluster_ctarank();
+    for (int q = off[pair]; q < off[pair + 1]; ++q) {
+        const int4 w = items[q];
+        const bool cut = w.w >= 0;
+        float *scr = cut ? d.p1_fix + (size_t)(2 * w.w + rank) * P1_SLOT : d.p1_acc + (size_t)blockIdx.x * P1_SLOT;
+        phase1_tile(maps, d, cur, w.x, w.y, w.z & 0xffff, w.z >> 16, cut ? d.p1_flag + 2 * w.w + rank : nullptr, g,
+                    tile, u, scr);
+    }
     phase1_tmem_free();
 }
 
@@ -991,7 +1056,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1) k_tc_ph
     float *scr = a.acc + (size_t)blockIdx.x * P1_SLOT;
     for (int q = a.p1_off[pair]; q < a.p1_off[pair + 1]; ++q) {
         const int4 w = a.items1[q];  // (network, mt, nt, cost)
-        phase1_tile(a.maps[w.x], a.devs[w.x], set_cur(a, w.x), w.y, w.z, g, tile, u, scr);
+        phase1_tile(a.maps[w.x], a.devs[w.x], set_cur(a, w.x), w.y, w.z, 0, 1 << 15, nullptr, g, tile, u, scr);
     }
     phase1_tmem_free();
 }
@@ -1726,6 +1791,9 @@ struct TcHost {
     TcMaps maps;
     int *sched_off = nullptr;  // [grid2 + 1] offsets into sched
     int *sched = nullptr;      // packed phase-2 items (see P2Item)
+    int *p1_off = nullptr;     // [grid1 / 2 + 1] offsets into p1_items
+    int4 *p1_items = nullptr;  // phase-1 pieces (see build_p1)
+    int clusters = 0;          // two-CTA clusters of phase 1 resident at once (occupancy calculator)
     int grid1 = 0, grid2 = 0;  // CTAs of the persistent phase-1 and phase-2 launches
 };
 
@@ -1843,6 +1911,80 @@ void build_schedule(const Dev &d, int pairs, std::vector<int> &off, std::vector<
     build_p2({&d}, pairs, TC_P2_SPEC[0], off, tiles, nets);
 }
 
+// Phase-1 pieces of one network for `pairs` persistent CTA pairs, as lists
+// (off, items) per pair; returns the number of tiles cut between two pairs.
+// Whole tiles in rounds of the gene-block-major order (pair p: tiles p,
+// p + pairs, ...) while every pair has one.  When the tile count is not a
+// multiple of `pairs`, the last full round and the partial one would leave
+// pairs idle at the end; their tiles are instead taken TF-block-major, so
+// that the pairs over the TF blocks of one gene block run side by side and
+// share C's rows in L2, and their MMA work is cut into equal shares at
+// chunk boundaries.  A tile straddling two shares becomes a head (chunks
+// 0 .. b - 1) and a tail (chunks b .. , R-num, the epilogue) on the next
+// pair, which waits for the head's flag; each entry's chunks are added in
+// the same order as in an uncut tile (the result is the same to the bit).
+// A pair runs its whole-tile rounds first (all pairs in step, so the TF
+// blocks of a gene block still read C's rows together), then its head, its
+// whole tiles of the cut rounds, and its tail last: a head waits for
+// nothing, so no tail waits on work that cannot run.  cut_ok is false when
+// not every pair is known to be resident at once (a tail could wait for a
+// head that cannot start).
+int build_p1(const Dev &d, int pairs, bool cut_ok, std::vector<int> &off, std::vector<int4> &items)
+{
+    const int nmt = d.Tp / 256, ntile = nmt * (d.Gp / 256);
+    const int nA = d.Gp / (d.fp8 ? 2 * BK : BK), nR = d.Tp / BK, nc = (nA + P1_CHUNK - 1) / P1_CHUNK;
+    pairs = std::max(1, std::min(pairs, ntile));
+    std::vector<std::vector<int4>> rounds(pairs), head(pairs), body(pairs), tail(pairs);
+    const bool cut = cut_ok && nc >= 2 && ntile > pairs && ntile % pairs != 0;
+    const int ndp = cut ? (ntile / pairs - 1) * pairs : ntile;
+    for (int q = 0; q < ndp; ++q)
+        rounds[q % pairs].push_back(make_int4(q % nmt, q / nmt, nc << 16, -1));
+    int cuts = 0;
+    if (cut) {
+        std::vector<std::pair<int, int>> sk;  // (mt, nt), TF-block-major
+        for (int q = ndp; q < ntile; ++q)
+            sk.push_back({q % nmt, q / nmt});
+        std::sort(sk.begin(), sk.end());
+        // MMA issue slots: a k-block is 4 MMAs of K = 16 per term (E4M3: K = 32, one term); the
+        // epilogue after the last chunk is counted as 64 slots
+        const long long wA = d.fp8 ? 4 : 4 * (d.split_b ? 3 : 2), wR = 4 * (d.split_b ? 3 : 2);
+        std::vector<long long> cost(nc);
+        long long per_tile = 0;
+        for (int c = 0; c < nc; ++c) {
+            cost[c] = wA * std::min(P1_CHUNK, nA - c * P1_CHUNK) + (c == nc - 1 ? wR * nR + 64 : 0);
+            per_tile += cost[c];
+        }
+        const double share = (double)per_tile * (double)sk.size() / pairs;
+        long long pos = 0;
+        for (const auto &t : sk) {
+            // owner of each chunk: the share holding its midpoint (at most two per tile: share >= one tile)
+            std::vector<int> own(nc);
+            for (int c = 0; c < nc; ++c) {
+                own[c] = std::min(pairs - 1, (int)(((double)pos + 0.5 * (double)cost[c]) / share));
+                pos += cost[c];
+            }
+            int b = 1;
+            while (b < nc && own[b] == own[0])
+                ++b;
+            if (b == nc) {
+                body[own[0]].push_back(make_int4(t.first, t.second, nc << 16, -1));
+            } else {
+                head[own[0]].push_back(make_int4(t.first, t.second, b << 16, cuts));
+                tail[own[b]].push_back(make_int4(t.first, t.second, b | nc << 16, cuts));
+                ++cuts;
+            }
+        }
+    }
+    off.assign(1, 0);
+    items.clear();
+    for (int p = 0; p < pairs; ++p) {
+        for (auto *l : {&rounds[p], &head[p], &body[p], &tail[p]})
+            items.insert(items.end(), l->begin(), l->end());
+        off.push_back((int)items.size());
+    }
+    return cuts;
+}
+
 cudaError_t set_smem_limits()
 {
     static bool done = false;
@@ -1873,6 +2015,36 @@ cudaError_t set_smem_limits()
     return cudaSuccess;
 }
 
+// CTA pairs of the phase-1 launch of one network (one per SM pair), and
+// whether all of them are resident at once (the occupancy calculator's count
+// of co-resident two-CTA clusters).
+cudaError_t phase1_pairs(int &pairs, bool &all_resident, int *clusters_out = nullptr)
+{
+    cudaError_t e = set_smem_limits();
+    int dev = 0, nsm = 0;
+    if (e || (e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)))
+        return e;
+    pairs = nsm / 2;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * pairs);
+    cfg.blockDim = dim3(THREADS1);
+    cfg.dynamicSmemBytes = phase1_smem();
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    all_resident = cudaOccupancyMaxActiveClusters(&clusters, (void *)k_tc_phase1, &cfg) == cudaSuccess &&
+                   clusters >= pairs;
+    cudaGetLastError();
+    if (clusters_out)
+        *clusters_out = clusters;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 // Phase-1 candidates: the order of a network's tiles (LPT over persistent pairs by main-loop length)
@@ -1882,6 +2054,32 @@ const char *const TC_P1_NAMES[TC_P1_CANDS] = {"tiles of a gene block together (C
 const char *const TC_P2_NAMES[TC_P2_CANDS] = {
     "LPT on MMA slots + 192", "LPT on max(MMA, HBM) + 48", "LPT on max(MMA, HBM) + 192",
     "LPT on max(MMA, HBM) + 192, heavy and light tiles alternating", "LPT on max(MMA, HBM) + 768"};
+
+int tc_phase1_plan(const Dev &d, int pairs, bool cut_ok, std::vector<int> &off, std::vector<int4> &items)
+{
+    return build_p1(d, pairs, cut_ok, off, items);
+}
+
+int tc_phase1_layout(const Dev &d, int *pairs, int *clusters)
+{
+    const TcHost *h = static_cast<const TcHost *>(d.tc_host);
+    if (!h)
+        return -1;
+    *pairs = h->grid1 / 2;
+    *clusters = h->clusters;
+    return d.p1_cuts;
+}
+
+int tc_phase1_cuts(const Dev &d)
+{
+    int pairs = 0;
+    bool resident = false;
+    if (phase1_pairs(pairs, resident))
+        return -1;
+    std::vector<int> off;
+    std::vector<int4> items;
+    return build_p1(d, pairs, resident, off, items);
+}
 
 bool tc_supported()
 {
@@ -1950,11 +2148,23 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales)
         std::vector<int> off, tiles;
         build_schedule(d, nsm / 2, off, tiles);  // one list per CTA pair
         h->grid2 = 2 * ((int)off.size() - 1);
-        h->grid1 = 2 * std::min(nsm / 2, (d.Tp / 256) * (d.Gp / 256));
+        int pairs = 0;
+        bool resident = false;
+        std::vector<int> off1;
+        std::vector<int4> items1;
+        if ((e = phase1_pairs(pairs, resident, &h->clusters)))
+            return e;
+        if (build_p1(d, pairs, resident, off1, items1) > d.p1_cuts)
+            return cudaErrorInvalidValue;  // the memory plan made fewer cut slots (cannot happen)
+        h->grid1 = 2 * ((int)off1.size() - 1);
         if ((e = cudaMalloc(&h->sched_off, off.size() * sizeof(int))) ||
             (e = cudaMalloc(&h->sched, tiles.size() * sizeof(int))) ||
             (e = cudaMemcpy(h->sched_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
-            (e = cudaMemcpy(h->sched, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice)))
+            (e = cudaMemcpy(h->sched, tiles.data(), tiles.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
+            (e = cudaMalloc(&h->p1_off, off1.size() * sizeof(int))) ||
+            (e = cudaMalloc(&h->p1_items, items1.size() * sizeof(int4))) ||
+            (e = cudaMemcpy(h->p1_off, off1.data(), off1.size() * sizeof(int), cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(h->p1_items, items1.data(), items1.size() * sizeof(int4), cudaMemcpyHostToDevice)))
             return e;
     }
     return cudaSuccess;
@@ -1966,6 +2176,8 @@ void tc_release(Dev &d)
     if (h) {
         cudaFree(h->sched_off);
         cudaFree(h->sched);
+        cudaFree(h->p1_off);
+        cudaFree(h->p1_items);
         delete h;
     }
     d.tc_host = nullptr;
@@ -1976,7 +2188,7 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
     const TcHost &h = *static_cast<const TcHost *>(d.tc_host);
     const TcMaps &m = h.maps;
     ke.mark(s);
-    k_tc_phase1<<<h.grid1, THREADS1, phase1_smem(), s>>>(m, d, cur);
+    k_tc_phase1<<<h.grid1, THREADS1, phase1_smem(), s>>>(m, d, cur, h.p1_items, h.p1_off);
     ke.mark(s);
     cudaError_t e = launch_reduce_wnorms(d, s);
     if (e)

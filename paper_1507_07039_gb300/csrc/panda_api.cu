@@ -183,6 +183,13 @@ int plan_memory(panda_ctx *c)
         int nsm = 0;
         CU(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device));
         DALLOC(d.p1_acc, (size_t)nsm * 128 * 256);
+        d.p1_cuts = tc_phase1_cuts(d);  // tiles cut between two pairs: a slot and a flag per CTA rank
+        if (d.p1_cuts < 0)
+            return set_err(c, PANDA_ECUDA, "cudaOccupancyMaxActiveClusters failed");
+        if (d.p1_cuts > 0) {
+            DALLOC(d.p1_fix, (size_t)d.p1_cuts * 2 * 128 * 256);
+            DALLOC(d.p1_flag, (size_t)d.p1_cuts * 2);
+        }
         if (d.fp8) {  // W.C and W^T.W on E4M3 copies; no BF16 copy of C
             for (int b = 0; b < 2; ++b) {
                 DALLOC(d.W8[b], Tp * Gp);
@@ -401,6 +408,8 @@ int drive_begin(panda_ctx *c, float alpha, double tol, int max_iter, bool use_gr
         return set_err(c, PANDA_EINVAL, "iteration count would exceed the supported maximum (65536)");
     h.active = max_iter > 0;
     h.stop_at = ds.start + max_iter;
+    if (h.status && c->d.p1_flag)  // a run that gave up may have left a cut tile's flag raised
+        CU(cudaMemsetAsync(c->d.p1_flag, 0, (size_t)c->d.p1_cuts * 2 * sizeof(int), c->stream));
     h.status = 0;
     h.converged = 0;
     h.alpha = alpha;
@@ -1463,6 +1472,47 @@ const char *panda_batch_schedule_name(int phase, int k)
     if (phase == 2 && k >= 0 && k < TC_P2_CANDS)
         return TC_P2_NAMES[k];
     return nullptr;
+}
+
+int panda_phase1_layout(const panda_ctx *c, int *pairs, int *clusters, int *cuts)
+{
+    if (!c || !tensor_prec(c->prec))
+        return set_err(nullptr, PANDA_EINVAL, "panda_phase1_layout: no tensor-core context");
+    int p = 0, k = 0;
+    const int n = tc_phase1_layout(c->d, &p, &k);
+    if (n < 0)
+        return set_err(nullptr, PANDA_EINVAL, "panda_phase1_layout: the context is not prepared");
+    if (pairs)
+        *pairs = p;
+    if (clusters)
+        *clusters = k;
+    if (cuts)
+        *cuts = n;
+    return 0;
+}
+
+int panda_phase1_plan(int T, int G, int prec, int pairs, int all_resident, int *pieces, int cap, int *n_pieces)
+{
+    if (T < 1 || G < 1 || !tensor_prec(prec) || pairs < 1 || !n_pieces || (cap > 0 && !pieces))
+        return set_err(nullptr, PANDA_EINVAL, "panda_phase1_plan: bad argument");
+    Dev d{};
+    d.T = T; d.G = G;
+    d.Tp = round_up(T, 2 * TILE); d.Gp = round_up(G, 2 * TILE);
+    d.split_b = prec == PANDA_BF16X2 ? 0 : 1;
+    d.fp8 = prec == PANDA_FP8MIX ? 1 : 0;
+    std::vector<int> off;
+    std::vector<int4> items;
+    const int cuts = tc_phase1_plan(d, pairs, all_resident != 0, off, items);
+    *n_pieces = (int)items.size();
+    int k = 0;
+    for (int p = 0; p + 1 < (int)off.size(); ++p)
+        for (int q = off[p]; q < off[p + 1]; ++q, ++k)
+            if (k < cap) {
+                const int4 w = items[q];
+                int *o = pieces + 6 * (size_t)k;
+                o[0] = p; o[1] = w.x; o[2] = w.y; o[3] = w.z & 0xffff; o[4] = w.z >> 16; o[5] = w.w;
+            }
+    return cuts;
 }
 
 const char *panda_batch_last_error(const panda_batch *b) { return b ? b->err.c_str() : g_create_error.c_str(); }

@@ -88,6 +88,10 @@ struct Dev {
     void *tc_host;               // host-side tensor maps of the split copies (tensor-core path)
     float *p1_acc;               // tensor-core phase 1: per CTA of its grid, a 128 x 256 slot for the
                                  // running sum of the availability numerator's chunks
+    float *p1_fix;               // per tile cut between two CTA pairs (at most one per pair), a
+                                 // 128 x 256 slot per CTA rank where its two pieces meet
+    int *p1_flag;                // per cut tile and CTA rank: its head's adds have landed
+    int p1_cuts;                 // cut tiles (slots and flag pairs above)
 };
 
 // Largest power of two s with s * bound <= 448 (the largest finite E4M3 value):
@@ -220,6 +224,16 @@ bool tc_supported();
 // fresh_scales: derive the FP8MIX scales from the state's norms (false: keep those restored)
 cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales = true);  // split copies of the state, tensor maps
 void tc_release(Dev &d);
+// Tiles of one network's phase 1 cut between two CTA pairs (each needs a
+// running-sum slot per CTA rank and a flag per rank); -1 on a CUDA error.
+int tc_phase1_cuts(const Dev &d);
+// The phase-1 launch of a prepared tensor-core context: CTA pairs, resident
+// two-CTA clusters; returns its cut tiles (-1: not prepared).
+int tc_phase1_layout(const Dev &d, int *pairs, int *clusters);
+// The phase-1 pieces of one network (Dev needs Tp, Gp, fp8, split_b) for
+// `pairs` CTA pairs: per pair p, items[off[p] .. off[p + 1]) of (mt, nt,
+// c0 | c1 << 16, cut or -1); returns the number of cut tiles.  Host only.
+int tc_phase1_plan(const Dev &d, int pairs, bool cut_ok, std::vector<int> &off, std::vector<int4> &items);
 cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEvents &ke);
 
 // A set of networks (tensor-core modes, same options) iterated by one launch

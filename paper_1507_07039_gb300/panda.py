@@ -79,6 +79,8 @@ def _load() -> ctypes.CDLL:
         "panda_batch_schedule": (i, [vp, pi, pi, ctypes.POINTER(ctypes.c_float), i,
                                      ctypes.POINTER(ctypes.c_float), i, pi]),
         "panda_batch_schedule_name": (ctypes.c_char_p, [i, i]),
+        "panda_phase1_plan": (i, [i, i, i, i, i, pi, i, pi]),
+        "panda_phase1_layout": (i, [vp, pi, pi, pi]),
         "panda_batch_destroy": (None, [vp]),
         "panda_destroy": (None, [vp]),
     }
@@ -295,6 +297,27 @@ def panda_measure_ffma_peak() -> float:
     t = ctypes.c_double(0.0)
     _check(lib.panda_measure_ffma_peak(ctypes.byref(t)))
     return t.value
+
+
+def panda_phase1_plan(T: int, G: int, prec: int, pairs: int, all_resident: bool = True):
+    """How phase 1 of a T x G network is spread over `pairs` CTA pairs (host
+    only): (number of cut tiles, int array of pieces with columns pair, mt,
+    nt, c0, c1, cut)."""
+    n = ctypes.c_int(0)
+    _check(lib.panda_phase1_plan(int(T), int(G), int(prec), int(pairs), int(bool(all_resident)), None, 0,
+                                 ctypes.byref(n)))
+    out = np.zeros((n.value, 6), np.int32)
+    cuts = _check(lib.panda_phase1_plan(int(T), int(G), int(prec), int(pairs), int(bool(all_resident)),
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n.value, ctypes.byref(n)))
+    return cuts, out
+
+
+def panda_phase1_layout(ctx) -> dict:
+    """The phase-1 launch of a tensor-core context: CTA pairs, resident
+    two-CTA clusters, cut tiles."""
+    p, k, n = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    _check(lib.panda_phase1_layout(ctx, ctypes.byref(p), ctypes.byref(k), ctypes.byref(n)), ctx)
+    return {"pairs": p.value, "clusters": k.value, "cuts": n.value}
 
 
 def panda_selftest_timeout() -> int:

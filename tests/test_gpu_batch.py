@@ -95,6 +95,26 @@ def test_batch_with_a_set_sized_network():
     print("\n250 x 15000 in a set, 2 iterations: " + ", ".join(f"{k} {v:.3e}" for k, v in e.items()))
 
 
+@pytest.mark.parametrize("prec", [1, 2, 3])
+def test_cut_tiles_give_the_bits_of_whole_tiles(prec):
+    """1000 TFs x 5200 genes: 84 phase-1 tiles on 76 CTA pairs, so a context
+    of its own cuts the tiles of its last rounds between two pairs at chunk
+    boundaries (panda_phase1_plan), while the set engine runs whole tiles.
+    The chunks of every entry are added in the same order either way: the
+    network alone and in a set of one agree bit for bit."""
+    from paper_1507_07039_gb300 import panda
+    W0, P0, C0 = gh.inputs("human1000x5200")
+    cuts, _ = panda.panda_phase1_plan(1000, 5200, prec, 76)
+    assert cuts > 0
+    with panda.PandaBatch([(W0, P0, C0)], prec=prec) as b:
+        _, iters, _ = b.run(0.1, 0.0, 3)
+        got = b.get(0)
+    assert list(iters) == [3]
+    single = gh.gpu_run(W0, P0, C0, prec, 0.1, 0.0, 3)
+    for a, g in zip((single["W"], single["P"], single["C"]), got):
+        assert np.array_equal(a, g), "a context's cut tiles differ from the set engine's whole tiles"
+
+
 @pytest.mark.parametrize("prec", [1, 3])
 def test_batch_diagonal_rule_d2(prec):
     """The set engine under rule D2 (its phase 2 also sums the new
