@@ -217,41 +217,26 @@ __device__ __forceinline__ void ld_rows4(const float *p, int ld, float4 (&v)[4])
         v[i] = *reinterpret_cast<const float4 *>(p + (size_t)(8 * i) * ld);
 }
 
-// 8 bytes from global memory, asking L2 to fetch the whole 128-byte line: a
-// warp's row segments here are 32 bytes, and the next sub-chunk reads the
-// rest of each line
-__device__ __forceinline__ uint2 ld8_l2line(const void *p)
+// 16 bytes from global memory, asking L2 to fetch the whole aligned 256-byte
+// block around them: a phase-2 epilogue thread reads its row's old values 32
+// bytes (16 entries) of each half at a time, and the 256-byte block holds the
+// rest of its row segment, which the next sub-chunks read
+__device__ __forceinline__ uint4 ld16_l2block(const void *p)
 {
-    uint2 v;
-    asm volatile("ld.global.L2::128B.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    uint4 v;
+    asm volatile("ld.global.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
     return v;
 }
 
-// As ld_rows4 for a matrix held as a BF16 split pair: four values hi + lo from
-// 8-byte loads of each half (the sum is exact in FP32)
-__device__ __forceinline__ void ld_rows4_split(const __nv_bfloat16 *h, const __nv_bfloat16 *l, int ld, float4 (&v)[4])
-{
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const size_t o = (size_t)(8 * i) * ld;
-        const uint2 a = ld8_l2line(h + o), b = ld8_l2line(l + o);
-        const float2 a0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.x));
-        const float2 a1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&a.y));
-        const float2 b0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&b.x));
-        const float2 b1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&b.y));
-        v[i] = make_float4(a0.x + b0.x, a0.y + b0.y, a1.x + b1.x, a1.y + b1.y);
-    }
-}
-
-// For a matrix held as a BF16 split pair: 8 consecutive values hi + lo of
-// rows p and p + 16 ld (16-byte loads of each half), into v[0..1] and v[2..3]
-__device__ __forceinline__ void ld_rows2x8_split(const __nv_bfloat16 *h, const __nv_bfloat16 *l, int ld,
-                                                 float4 (&v)[4])
+// For a matrix held as a BF16 split pair: 16 consecutive values hi + lo of one
+// row (the sum is exact in FP32), into v[0..3]
+__device__ __forceinline__ void ld_row16_split(const __nv_bfloat16 *h, const __nv_bfloat16 *l, float4 (&v)[4])
 {
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
-        const size_t o = (size_t)(16 * i) * ld;
-        const uint4 a = *reinterpret_cast<const uint4 *>(h + o), b = *reinterpret_cast<const uint4 *>(l + o);
+        const uint4 a = ld16_l2block(h + 8 * i), b = ld16_l2block(l + 8 * i);
         const uint32_t av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
         float f[8];
 #pragma unroll
@@ -1413,17 +1398,17 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
             const int k = m0 + r, k0 = m0 + wq * 32;
             const bool krow = k < nn;  // rows past the network (last block's padding) hold nothing
             const float nk_ = krow ? nrm[k] : 0.0f;
-            // old values, loaded coalesced (8 rows x 64 B per load): lane l takes columns
-            // 4 (l & 3) .. + 3 of the warp's rows (l >> 2) + 8 i, i = 0..3 (rows past the network
-            // are padding inside the array; their values are never used).  A split-held C: lane l
-            // takes columns 8 (l & 1) .. + 7 of rows (l >> 1) + 16 i, i = 0..1, 16 bytes of each half
-            const size_t xo = sst ? (size_t)(k0 + (lane >> 1)) * ld + n0 + 8 * (lane & 1)
-                                  : (size_t)(k0 + (lane >> 2)) * ld + n0 + 4 * (lane & 3);
+            // old values (rows past the network are padding inside the array; their values are never
+            // used).  FP32: loaded coalesced (8 rows x 64 B per load), lane l takes columns
+            // 4 (l & 3) .. + 3 of the warp's rows (l >> 2) + 8 i, i = 0..3, and each lane gets its own
+            // row through the staging block.  A split-held C: each lane loads its own row, 32 bytes of
+            // each half per sub-chunk, L2 fetching the row's 256-byte block at the first
+            const size_t xo = sst ? (size_t)k * ld + n0 : (size_t)(k0 + (lane >> 2)) * ld + n0 + 4 * (lane & 3);
             const float *xblk = sst ? nullptr : X + xo;
             float4 nxt[4];
             if (n0 + c_begin * 16 < ld) {
                 if (sst)
-                    ld_rows2x8_split(Xh + xo + c_begin * 16, Xl + xo + c_begin * 16, ld, nxt);
+                    ld_row16_split(Xh + xo + c_begin * 16, Xl + xo + c_begin * 16, nxt);
                 else
                     ld_rows4(xblk + c_begin * 16, ld, nxt);
             }
@@ -1444,21 +1429,29 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 const int cc = c * 16, j0 = n0 + cc;
                 const bool inside = krow && j0 < ld;
                 float old[16], acc[16];
-                // old values to this lane's own row through the staging block
+                if (sst) {  // this lane's own row
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    float *b = sst ? blk + ((lane >> 1) + 16 * (i >> 1)) * 17 + 8 * (lane & 1) + 4 * (i & 1)
-                                   : blk + ((lane >> 2) + 8 * i) * 17 + 4 * (lane & 3);
-                    b[0] = nxt[i].x; b[1] = nxt[i].y; b[2] = nxt[i].z; b[3] = nxt[i].w;
+                    for (int i = 0; i < 4; ++i) {
+                        old[4 * i] = inside ? nxt[i].x : 0.0f;
+                        old[4 * i + 1] = inside ? nxt[i].y : 0.0f;
+                        old[4 * i + 2] = inside ? nxt[i].z : 0.0f;
+                        old[4 * i + 3] = inside ? nxt[i].w : 0.0f;
+                    }
+                } else {  // to this lane's own row through the staging block
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float *b = blk + ((lane >> 2) + 8 * i) * 17 + 4 * (lane & 3);
+                        b[0] = nxt[i].x; b[1] = nxt[i].y; b[2] = nxt[i].z; b[3] = nxt[i].w;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        old[q] = inside ? blk[lane * 17 + q] : 0.0f;
+                    __syncwarp();  // the block takes the new values next
                 }
-                __syncwarp();
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    old[q] = inside ? blk[lane * 17 + q] : 0.0f;
-                __syncwarp();  // the block takes the new values next
                 if (c + 1 < c_end && j0 + 16 < ld) {  // next sub-chunk's old values, in flight meanwhile
                     if (sst)
-                        ld_rows2x8_split(Xh + xo + (c + 1) * 16, Xl + xo + (c + 1) * 16, ld, nxt);
+                        ld_row16_split(Xh + xo + (c + 1) * 16, Xl + xo + (c + 1) * 16, nxt);
                     else
                         ld_rows4(xblk + (c + 1) * 16, ld, nxt);
                 }
