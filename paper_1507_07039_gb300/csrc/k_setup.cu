@@ -319,6 +319,27 @@ __global__ void k_row_norms(const float *__restrict__ X, int rows, int cols, int
     }
 }
 
+// out[j] = sum_i X[i][j]^2 over the first `rows` rows: the squared column
+// norms of a row-major matrix without its transpose.  Thread j walks column
+// j down the rows (a warp's loads are 32 consecutive columns of one row),
+// compensated FP32 pairs folded into an FP64 total every 256 rows.
+__global__ void k_col_norms(const float *__restrict__ X, int rows, int cols, int ld, float *out)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= cols)
+        return;
+    double tot = 0.0;
+    for (int r0 = 0; r0 < rows; r0 += 256) {
+        float acc = 0.0f, cmp = 0.0f;
+        const int re = min(rows, r0 + 256);
+#pragma unroll 4
+        for (int r = r0; r < re; ++r)
+            sq_add(X[(size_t)r * ld + j], acc, cmp);
+        tot += (double)acc + (double)cmp;
+    }
+    out[j] = (float)tot;
+}
+
 __global__ void k_scan_nonfinite(const float *__restrict__ X, long long n, int *flag)
 {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -512,6 +533,12 @@ cudaError_t launch_row_norms(const float *X, int rows, int cols, int ld, const d
     if (!rows_aligned(X, ld))
         return cudaErrorInvalidValue;
     k_row_norms<<<ceil_div(rows * 32, 256), 256, 0, s>>>(X, rows, cols, ld, diag, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_col_norms(const float *X, int rows, int cols, int ld, float *out, cudaStream_t s)
+{
+    k_col_norms<<<ceil_div(cols, 256), 256, 0, s>>>(X, rows, cols, ld, out);
     return cudaGetLastError();
 }
 

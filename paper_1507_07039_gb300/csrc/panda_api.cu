@@ -135,7 +135,8 @@ int plan_memory(panda_ctx *c)
     d.c_split = (c->prec == PANDA_BF16X3 || c->prec == PANDA_BF16X2) ? 1 : 0;
     for (int b = 0; b < 2; ++b) {
         DALLOC(d.W[b], Tp * Gp);
-        DALLOC(d.Wt[b], Gp * Tp);
+        if (!d.c_split)  // the FP32 path's operand, FP8MIX's source of its E4M3 transposes
+            DALLOC(d.Wt[b], Gp * Tp);
     }
     DALLOC(d.Poff, Tp * Tp);
     if (!d.c_split)
@@ -308,9 +309,13 @@ int derive_state(panda_ctx *c, bool split_diag)
         CU(launch_split_diag(d.Poff, c->T, c->Tp, d.pd, d.pdf, c->stream));
         CU(launch_split_diag(d.Coff, c->G, c->Gp, d.cd, d.cdf, c->stream));
     }
-    CU(launch_transpose(d.W[c->cur], c->Tp, c->Gp, d.Wt[c->cur], c->stream));
     CU(launch_row_norms(d.W[c->cur], c->T, c->G, c->Gp, nullptr, d.rsqW, c->stream));
-    CU(launch_row_norms(d.Wt[c->cur], c->G, c->T, c->Tp, nullptr, d.csqW, c->stream));  // columns of W
+    if (d.Wt[c->cur]) {
+        CU(launch_transpose(d.W[c->cur], c->Tp, c->Gp, d.Wt[c->cur], c->stream));
+        CU(launch_row_norms(d.Wt[c->cur], c->G, c->T, c->Tp, nullptr, d.csqW, c->stream));  // columns of W
+    } else {
+        CU(launch_col_norms(d.W[c->cur], c->T, c->G, c->Gp, d.csqW, c->stream));
+    }
     CU(launch_row_norms(d.Poff, c->T, c->T, c->Tp, d.pd, d.rsqP, c->stream));
     CU(launch_row_norms(d.Coff, c->G, c->G, c->Gp, d.cd, d.csqC, c->stream));
     if (tensor_prec(c->prec))
@@ -995,7 +1000,8 @@ int panda_load(panda_ctx *c, const void *buf, long long bytes)
         p += it.bytes;
     }
     Dev &d = c->d;
-    CU(launch_transpose(d.W[c->cur], c->Tp, c->Gp, d.Wt[c->cur], c->stream));
+    if (d.Wt[c->cur])
+        CU(launch_transpose(d.W[c->cur], c->Tp, c->Gp, d.Wt[c->cur], c->stream));
     CU(launch_diag_to_float(d.pd, d.pdf, c->T, c->stream));
     CU(launch_diag_to_float(d.cd, d.cdf, c->G, c->stream));
     if (tensor_prec(c->prec))

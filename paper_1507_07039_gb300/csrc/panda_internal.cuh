@@ -49,7 +49,7 @@ enum : int { ST_NONFINITE = 1, ST_TIMEOUT = 2 };
 struct Dev {
     int T, G, Tp, Gp, nbT, nbG;  // true sizes, padded sizes, 128-blocks
     int diag;                    // panda_diag
-    float *W[2], *Wt[2];
+    float *W[2], *Wt[2];         // Wt: FP32 and FP8MIX only (NULL under BF16X3 and BF16X2)
     float *Poff, *Coff;
     double *pd, *cd;
     float *pdf, *cdf;            // FP32 copies of the diagonals for epilogues
@@ -171,6 +171,8 @@ cudaError_t launch_zscore(float *X, int rows, int cols, int ld, double *stats, d
                           cudaStream_t s);
 cudaError_t launch_split_diag(float *X, int n, int ld, double *d, float *df, cudaStream_t s);
 cudaError_t launch_transpose(const float *X, int rows_p, int cols_p, float *Y, cudaStream_t s);
+// out[j] = sum over the first `rows` rows of X[i][j]^2 (squared column norms, no transpose)
+cudaError_t launch_col_norms(const float *X, int rows, int cols, int ld, float *out, cudaStream_t s);
 cudaError_t launch_row_norms(const float *X, int rows, int cols, int ld, const double *diag,
                              float *out, cudaStream_t s);
 cudaError_t launch_diag_to_float(const double *d, float *df, int n, cudaStream_t s);
