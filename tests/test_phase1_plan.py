@@ -106,3 +106,45 @@ def test_bad_arguments_are_refused():
     for args in ((0, 10, 1, 76), (10, 0, 1, 76), (10, 10, 0, 76), (10, 10, 1, 0)):
         with pytest.raises(panda.PandaError):
             panda.panda_phase1_plan(*args)
+
+
+@pytest.mark.parametrize("T,G,pairs", [(1000, 17000, 76), (1000, 5200, 76), (700, 23000, 76), (1600, 30000, 76),
+                                       (1000, 17000, 3), (1000, 17000, 7)])
+def test_pieces_run_to_the_end_and_balance(T, G, pairs):
+    """Every pair runs its list in order; a tail piece may not start before
+    the head of its tile has finished (a stricter rule than the kernel's,
+    which waits only before touching the running sum).  Played out in MMA
+    slots, every list ends (no pair waits on a piece that waits itself) and
+    the last pair ends within 2% of an even split of the work whenever tiles
+    were cut (within one chunk's worth of it for coarse chunks)."""
+    from paper_1507_07039_gb300 import panda
+    cuts, pc = panda.panda_phase1_plan(T, G, 1, pairs)
+    nmt, nnt, nc, cost = chunk_costs(T, G, 1)
+    lists = {}
+    for row in pc:
+        lists.setdefault(int(row[0]), []).append(tuple(int(x) for x in row[1:]))
+    head_end, pos, t = {}, {p: 0 for p in lists}, {p: 0.0 for p in lists}
+    for _ in range(sum(len(v) for v in lists.values()) + 1):
+        moved = False
+        for p, items in lists.items():
+            while pos[p] < len(items):
+                mt, nt, c0, c1, cut = items[pos[p]]
+                start = t[p]
+                if cut >= 0 and c0 > 0:
+                    if cut not in head_end:
+                        break
+                    start = max(start, head_end[cut])
+                t[p] = start + sum(cost[c0:c1])
+                if cut >= 0 and c0 == 0:
+                    head_end[cut] = t[p]
+                pos[p] += 1
+                moved = True
+        if not moved:
+            break
+    assert all(pos[p] == len(items) for p, items in lists.items()), "a pair never finished its list"
+    total = sum(sum(cost) for _ in range(nmt * nnt))
+    ideal = total / len(lists)
+    if cuts:
+        assert max(t.values()) <= ideal * 1.02 + max(cost)
+    if T == 1000 and G == 17000 and pairs == 76:
+        assert max(t.values()) <= ideal * 1.02
