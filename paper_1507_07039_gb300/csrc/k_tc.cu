@@ -1053,7 +1053,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1) k_tc_ph
 // the even CTA issues cta_group::2 MMAs (M = N = 256) whose result rows
 // 128 r .. + 127 land in CTA r's TMEM.  Two accumulators of 256 columns
 // alternate, so the epilogue of one tile overlaps the MMAs of the next.
-// Warps: 0 TMA, 1 MMA (even CTA), then EPI2 epilogue warps (EPI2 / 4 per
+// Warps: 0 TMA, 1 MMA (even CTA), then EPI epilogue warps (EPI / 4 per
 // TMEM lane quarter, splitting the 256 columns in 16-column sub-chunks).
 //
 // Row partial sums for Eq. 6 use separate slot ranges so the two CTAs of a
@@ -1061,24 +1061,30 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS1, 1) k_tc_ph
 // 256 columns) goes to slot bn, the column role (a column of the tile, summed
 // over this CTA's 128 rows) to slot nb + 2 bm + r.
 // ---------------------------------------------------------------------------
-// Epilogue warps: EPI2 / 4 per TMEM lane quarter.  The epilogue bounds phase
-// 2 (its C' tiles have K = T, so a tile's MMAs take about as long as its
-// 256 x 256 outputs take to finish); twelve warps with two operand stages
-// (64 KB each) ran phase 2 5% faster than eight with three at 1000 x 17000.
-constexpr int EPI2 = 12;
-constexpr int THREADS2 = 64 + 32 * EPI2;
+// Epilogue warps: EPI / 4 per TMEM lane quarter, a template parameter of the
+// phase-2 kernels.  A C' tile has K = T, so its MMAs take about as long as its
+// 256 x 256 outputs take to finish: where the MMAs are the shorter part
+// (T up to about 1300 in BF16X3), twelve epilogue warps with two 64 KB
+// operand stages ran phase 2 5% faster than eight with three at 1000 x 17000;
+// where they are the longer part, the third stage keeps them fed (1600 x
+// 30000: 3.0 ms against 3.7 with two).  p2_epi picks one per launch.
 constexpr int N2 = 256;                    // tile edge
 constexpr uint32_t STAGE2 = 4 * A_BYTES;   // per CTA: A hi, A lo, B hi, B lo (128 rows each)
 
 // named barrier among the phase-2 epilogue warps
-__device__ __forceinline__ void epi_bar_p2() { asm volatile("bar.sync 2, %0;" ::"n"(32 * EPI2) : "memory"); }
+template <int EPI>
+__device__ __forceinline__ void epi_bar_p2()
+{
+    asm volatile("bar.sync 2, %0;" ::"n"(32 * EPI) : "memory");
+}
 
-template <bool SIM>
+template <bool SIM, int EPI>
 struct P2Cfg {
+    static constexpr int THREADS = 64 + 32 * EPI;      // TMA warp, MMA warp, epilogue warps
     static constexpr int NS = SIM ? 3 : 2;             // sums per row: x, x^2 (and v^2 under D2)
-    static constexpr int ST = EPI2 > 8 || SIM ? 2 : 3;  // pipeline stages that fit beside the epilogue buffers
+    static constexpr int ST = EPI > 8 || SIM ? 2 : 3;  // pipeline stages that fit beside the epilogue buffers
     static constexpr size_t COLRED = 4 * NS * N2;      // [quarter][sum][column] floats
-    static constexpr size_t ROWRED = (EPI2 / 4) * NS * 128;  // [column part][sum][row] floats
+    static constexpr size_t ROWRED = (EPI / 4) * NS * 128;  // [column part][sum][row] floats
     static constexpr size_t COLNRM = N2;               // the tile's column norms
     static constexpr size_t BLK = 32 * 17;             // per epilogue warp: 32 x 16 staging block (padded)
 };
@@ -1125,12 +1131,12 @@ struct Sync2T {
     int abort, issued, consumed;
 };
 
-template <bool SIM>
+template <bool SIM, int EPI>
 constexpr size_t phase2_smem()
 {
-    using C = P2Cfg<SIM>;
+    using C = P2Cfg<SIM, EPI>;
     return 1024 + (size_t)C::ST * STAGE2 + ((sizeof(Sync2T<C::ST>) + 15) & ~size_t(15)) +
-           (C::COLRED + C::ROWRED + C::COLNRM + EPI2 * C::BLK) * sizeof(float);
+           (C::COLRED + C::ROWRED + C::COLNRM + EPI * C::BLK) * sizeof(float);
 }
 
 // Where phase 2 finds the network of each scheduled tile: one network given
@@ -1163,10 +1169,10 @@ struct P2Set {
 // tiles are skipped by every role alike (its control block does not change
 // during the launch), so the stage and accumulator counters stay in step.
 // ctl: where a timed-out wait outside any tile is reported.
-template <bool SIM_SIGMA, class Src>
+template <bool SIM_SIGMA, int EPI, class Src>
 __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
 {
-    using Cfg = P2Cfg<SIM_SIGMA>;
+    using Cfg = P2Cfg<SIM_SIGMA, EPI>;
     constexpr int ST2 = Cfg::ST, NS = Cfg::NS;
     using Sync2 = Sync2T<ST2>;
     extern __shared__ uint8_t smem_raw[];
@@ -1189,7 +1195,7 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(&sy.tfull[q], 1);
-            mbar_init(&sy.tempty[q], 2 * EPI2);
+            mbar_init(&sy.tempty[q], 2 * EPI);
         }
         sy.abort = 0;
         sy.issued = 0;
@@ -1320,8 +1326,8 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
             sy.consumed = g;
         }
     } else {  // ---- epilogue: warps 2..9 of both CTAs ----
-        // the EPI2 / 4 warps of a lane quarter split its 16 sub-chunks of 16 columns
-        constexpr int PARTS = EPI2 / 4;
+        // the EPI / 4 warps of a lane quarter split its 16 sub-chunks of 16 columns
+        constexpr int PARTS = EPI / 4;
         const int e = warp - 2, wq = warp & 3, third = e >> 2;
         const int c_begin = (16 * third) / PARTS, c_end = (16 * (third + 1)) / PARTS;
         const int r = wq * 32 + lane;  // row of this CTA's 128-row half
@@ -1412,7 +1418,7 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 else
                     ld_rows4(xblk + c_begin * 16, ld, nxt);
             }
-            epi_bar_p2();
+            epi_bar_p2<EPI>();
             // on a timed-out wait every epilogue warp still runs the named barriers below
             const bool live = wait_bounded(&sy.tfull[buf], (uint32_t)(idx >> 1) & 1u, &sy.abort, d.ctl) &&
                               !*(volatile int *)&sy.abort;
@@ -1670,7 +1676,7 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
             rowred[(third * NS + 1) * 128 + r] = r2;
             if (SIM_SIGMA)
                 rowred[(third * NS + 2) * 128 + r] = rv;
-            epi_bar_p2();
+            epi_bar_p2<EPI>();
             if (live) {
 #pragma unroll
                 for (int w = 0; w < 3; ++w) {
@@ -1692,7 +1698,7 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                     }
                 }
             }
-            epi_bar_p2();
+            epi_bar_p2<EPI>();
         }
     }
     tc_fence_before();
@@ -1707,20 +1713,20 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
     }
 }
 
-template <bool SIM_SIGMA>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1)
+template <bool SIM_SIGMA, int EPI>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EPI, 1)
     k_tc_phase2(const __grid_constant__ TcMaps maps, const __grid_constant__ Dev d, int cur,
                 const int *__restrict__ sched_off, const int *__restrict__ sched)
 {
     if (!d.ctl->active)  // both CTAs of a pair see the same value and leave together
         return;
-    phase2_pair<SIM_SIGMA>(P2One{maps, d, cur, sched_off, sched}, d.ctl);
+    phase2_pair<SIM_SIGMA, EPI>(P2One{maps, d, cur, sched_off, sched}, d.ctl);
 }
 
-template <bool SIM_SIGMA>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS2, 1) k_tc_phase2_set(const SetArgs a)
+template <bool SIM_SIGMA, int EPI>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(64 + 32 * EPI, 1) k_tc_phase2_set(const SetArgs a)
 {
-    phase2_pair<SIM_SIGMA>(P2Set{a, a.sched_off, a.sched}, a.devs[0].ctl);
+    phase2_pair<SIM_SIGMA, EPI>(P2Set{a, a.sched_off, a.sched}, a.devs[0].ctl);
 }
 
 // every network's control block into one array (one read-back per chunk of a set)
@@ -1792,6 +1798,7 @@ struct TcHost {
     int4 *p1_items = nullptr;  // phase-1 pieces (see build_p1)
     int clusters = 0;          // two-CTA clusters of phase 1 resident at once (occupancy calculator)
     int grid1 = 0, grid2 = 0;  // CTAs of the persistent phase-1 and phase-2 launches
+    int epi2 = 12;             // epilogue warps of the phase-2 kernel (p2_epi)
 };
 
 // Cost of a phase-2 tile in MMA issue slots (a BF16 MMA of K = 16 and an E4M3
@@ -1911,9 +1918,10 @@ void build_schedule(const Dev &d, int pairs, std::vector<int> &off, std::vector<
 // Phase-1 pieces of one network for `pairs` persistent CTA pairs, as lists
 // (off, items) per pair; returns the number of tiles cut between two pairs.
 // Whole tiles in rounds of the gene-block-major order (pair p: tiles p,
-// p + pairs, ...) while every pair has one.  When the tile count is not a
-// multiple of `pairs`, the last full round and the partial one would leave
-// pairs idle at the end; their tiles are instead taken TF-block-major, so
+// p + pairs, ...) while every pair has one.  When the tile count leaves the
+// last round more than about 1/20 of the work short (some pairs idle at the
+// end), the tiles of the last full round and the partial one are instead
+// taken TF-block-major, so
 // that the pairs over the TF blocks of one gene block run side by side and
 // share C's rows in L2, and their MMA work is cut into equal shares at
 // chunk boundaries.  A tile straddling two shares becomes a head (chunks
@@ -1932,7 +1940,11 @@ int build_p1(const Dev &d, int pairs, bool cut_ok, std::vector<int> &off, std::v
     const int nA = d.Gp / (d.fp8 ? 2 * BK : BK), nR = d.Tp / BK, nc = (nA + P1_CHUNK - 1) / P1_CHUNK;
     pairs = std::max(1, std::min(pairs, ntile));
     std::vector<std::vector<int4>> rounds(pairs), head(pairs), body(pairs), tail(pairs);
-    const bool cut = cut_ok && nc >= 2 && ntile > pairs && ntile % pairs != 0;
+    // whole tiles leave the busiest pair ceil(ntile / pairs) tiles against ntile / pairs on average;
+    // under 5% more, cutting costs more than it saves (the cut rounds share C's rows in L2 less
+    // well: 1600 x 30000, 1.2% to gain, ran phase 1 5% slower cut)
+    const int most = (ntile + pairs - 1) / pairs;
+    const bool cut = cut_ok && nc >= 2 && ntile > pairs && (double)most * pairs > 1.05 * ntile;
     const int ndp = cut ? (ntile / pairs - 1) * pairs : ntile;
     for (int q = 0; q < ndp; ++q)
         rounds[q % pairs].push_back(make_int4(q % nmt, q / nmt, nc << 16, -1));
@@ -1982,6 +1994,41 @@ int build_p1(const Dev &d, int pairs, bool cut_ok, std::vector<int> &off, std::v
     return cuts;
 }
 
+template <bool SIM, int EPI>
+cudaError_t phase2_smem_limits()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_tc_phase2<SIM, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)phase2_smem<SIM, EPI>());
+    return e ? e
+             : cudaFuncSetAttribute(k_tc_phase2_set<SIM, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)phase2_smem<SIM, EPI>());
+}
+
+// Epilogue warps of phase 2 for networks whose C' tiles take mma_slots MMA
+// issue slots each (the largest over a set): 12 (two operand stages) while
+// the MMAs are shorter than the epilogue, about 290 slots of the dense peak
+// at 1000 x 17000 (1000 x 17000 under BF16X3: 192 slots), else 8 (three
+// stages; 1600 x 30000: 336 slots)
+int p2_epi(long long mma_slots) { return mma_slots > 256 ? 8 : 12; }
+
+// One phase-2 launch of EPI epilogue warps
+template <int EPI, class... Args>
+void launch_p2_one(bool sim, int grid, cudaStream_t s, const Args &...args)
+{
+    if (sim)
+        k_tc_phase2<true, EPI><<<grid, P2Cfg<true, EPI>::THREADS, phase2_smem<true, EPI>(), s>>>(args...);
+    else
+        k_tc_phase2<false, EPI><<<grid, P2Cfg<false, EPI>::THREADS, phase2_smem<false, EPI>(), s>>>(args...);
+}
+template <int EPI>
+void launch_p2_set(bool sim, int grid, cudaStream_t s, const SetArgs &a)
+{
+    if (sim)
+        k_tc_phase2_set<true, EPI><<<grid, P2Cfg<true, EPI>::THREADS, phase2_smem<true, EPI>(), s>>>(a);
+    else
+        k_tc_phase2_set<false, EPI><<<grid, P2Cfg<false, EPI>::THREADS, phase2_smem<false, EPI>(), s>>>(a);
+}
+
 cudaError_t set_smem_limits()
 {
     static bool done = false;
@@ -1991,16 +2038,8 @@ cudaError_t set_smem_limits()
     if ((e = cudaFuncSetAttribute(k_tc_phase1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)phase1_smem())) ||
         (e = cudaFuncSetAttribute(k_tc_phase1_set, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)phase1_smem())) ||
-        (e = cudaFuncSetAttribute(k_tc_phase2_set<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)phase2_smem<false>())) ||
-        (e = cudaFuncSetAttribute(k_tc_phase2_set<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)phase2_smem<true>())))
-        return e;
-    if ((e = cudaFuncSetAttribute(k_tc_phase2<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)phase2_smem<false>())))
-        return e;
-    if ((e = cudaFuncSetAttribute(k_tc_phase2<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)phase2_smem<true>())))
+        (e = phase2_smem_limits<false, 8>()) || (e = phase2_smem_limits<true, 8>()) ||
+        (e = phase2_smem_limits<false, 12>()) || (e = phase2_smem_limits<true, 12>()))
         return e;
     constexpr size_t st_smem = 1024 + 3 * (4 * A_BYTES) + sizeof(Sync<3>) + 16;
     if ((e = cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)st_smem)))
@@ -2145,6 +2184,7 @@ cudaError_t tc_prepare(Dev &d, cudaStream_t s, bool fresh_scales)
         std::vector<int> off, tiles;
         build_schedule(d, nsm / 2, off, tiles);  // one list per CTA pair
         h->grid2 = 2 * ((int)off.size() - 1);
+        h->epi2 = p2_epi(tile_cost(d, false, 0));
         int pairs = 0;
         bool resident = false;
         std::vector<int> off1;
@@ -2191,10 +2231,10 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
     if (e)
         return e;
     ke.mark(s);
-    if (d.diag == 2)
-        k_tc_phase2<true><<<h.grid2, THREADS2, phase2_smem<true>(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
+    if (h.epi2 == 8)
+        launch_p2_one<8>(d.diag == 2, h.grid2, s, m, d, cur ^ 1, h.sched_off, h.sched);
     else
-        k_tc_phase2<false><<<h.grid2, THREADS2, phase2_smem<false>(), s>>>(m, d, cur ^ 1, h.sched_off, h.sched);
+        launch_p2_one<12>(d.diag == 2, h.grid2, s, m, d, cur ^ 1, h.sched_off, h.sched);
     ke.mark(s);
     return launch_fin_tail(d, s, ke);
 }
@@ -2202,6 +2242,7 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
 // ---- sets of networks: one launch per phase over all networks' tiles ---------------
 struct TcSet {
     int n = 0, diag = 0, pairs = 0;
+    int epi2 = 12;            // epilogue warps of the phase-2 kernel (p2_epi over the largest C' tile)
     Dev *devs = nullptr;      // device copies of the networks' Dev
     TcMaps *maps = nullptr;   // their tensor maps
     int *parity = nullptr;
@@ -2242,6 +2283,10 @@ cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out)
     TcSet *t = new TcSet;
     t->n = (int)ds.size();
     t->diag = ds[0]->diag;
+    long long slots = 0;
+    for (const Dev *d : ds)
+        slots = std::max<long long>(slots, tile_cost(*d, false, 0));
+    t->epi2 = p2_epi(slots);
     std::vector<Dev> hd;
     std::vector<TcMaps> hm;
     std::vector<int2> bl;
@@ -2315,10 +2360,10 @@ cudaError_t tc_set_launch(TcSet *t, int p1, int p2, cudaStream_t s, cudaEvent_t 
         return e;
     if (ev1)
         cudaEventRecord(ev1, s);
-    if (t->diag == 2)
-        k_tc_phase2_set<true><<<2 * c.pairs, THREADS2, phase2_smem<true>(), s>>>(a);
+    if (t->epi2 == 8)
+        launch_p2_set<8>(t->diag == 2, 2 * c.pairs, s, a);
     else
-        k_tc_phase2_set<false><<<2 * c.pairs, THREADS2, phase2_smem<false>(), s>>>(a);
+        launch_p2_set<12>(t->diag == 2, 2 * c.pairs, s, a);
     if (ev2)
         cudaEventRecord(ev2, s);
     return launch_fin_tail_set(t->devs, t->blocks, t->nblocks, t->n, s);
