@@ -305,8 +305,9 @@ const char *panda_batch_schedule_name(int phase, int k);
  * each 256 x 256 tile sums the availability numerator W.C over all genes in
  * chunks of 32 k-blocks (64 genes each; 128 under PANDA_FP8MIX), then the
  * responsibility numerator and the epilogue.  Whole tiles run in rounds;
- * when the tile count is not a multiple of pairs, the tiles of the last two
- * rounds are cut at chunk boundaries into equal shares of MMA work.  A cut
+ * when that leaves the busiest pair more than 5% above the average, the
+ * tiles of the last two rounds are cut at chunk boundaries into equal
+ * shares of MMA work.  A cut
  * tile's head (chunks 0 .. b - 1) runs first on its pair, its tail (chunks
  * b .. n - 1, the responsibility numerator, the epilogue) last on another,
  * which waits for the head: all_resident = 0 (not every pair known to be

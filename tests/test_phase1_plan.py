@@ -2,8 +2,9 @@
 persistent CTA pairs: panda_phase1_plan is host code, so these run on the CPU.
 
 Every 256 x 256 tile's availability sum is cut into chunks of 32 k-blocks;
-whole tiles run in rounds, and when the tile count is not a multiple of the
-pairs the last two rounds are cut at chunk boundaries into equal shares.
+whole tiles run in rounds, and when that leaves the busiest pair more than 5%
+above the average the last two rounds are cut at chunk boundaries into equal
+shares.
 Checked: every chunk of every tile is computed exactly once, a cut tile has
 exactly two pieces on two different pairs that share one cut index, a head
 piece (which others wait for) runs on its pair before anything that waits and
@@ -89,6 +90,13 @@ def test_human_sized_network_is_balanced():
     cuts, bal, whole = check_plan(1000, 17000, 1, 76)
     assert whole == pytest.approx(4 / (268 / 76))
     assert cuts > 0 and bal < 1.01
+
+
+def test_no_cuts_where_whole_tiles_are_nearly_even():
+    """1600 x 30000: 7 x 118 = 826 tiles on 76 pairs, the busiest pair 1.2%
+    above the average: whole tiles only."""
+    cuts, bal, whole = check_plan(1600, 30000, 1, 76)
+    assert cuts == 0 and whole == pytest.approx(11 / (826 / 76))
 
 
 def test_no_cuts_without_co_resident_pairs():
