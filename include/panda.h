@@ -307,10 +307,10 @@ const char *panda_batch_schedule_name(int phase, int k);
  * responsibility numerator and the epilogue.  Whole tiles run in rounds;
  * when that leaves the busiest pair more than 5% above the average, the
  * tiles of the last two rounds are cut at chunk boundaries into equal
- * shares of MMA work.  A cut
- * tile's head (chunks 0 .. b - 1) runs first on its pair, its tail (chunks
- * b .. n - 1, the responsibility numerator, the epilogue) last on another,
- * which waits for the head: all_resident = 0 (not every pair known to be
+ * shares of MMA work.  A cut tile's head (chunks 0 .. b - 1) runs on its
+ * pair right after the whole-tile rounds, its tail (chunks b .. n - 1, the
+ * responsibility numerator, the epilogue) last on another pair, which waits
+ * (bounded) for the head: all_resident = 0 (not every pair known to be
  * resident at once) makes no cuts.  Up to cap pieces are written to pieces,
  * six ints each, in the order each pair runs them, pair by pair: pair, TF
  * block mt, gene block nt, first chunk c0, end chunk c1 (c1 = n for a piece
