@@ -1869,15 +1869,20 @@ struct P2Spec {
 };
 const P2Spec TC_P2_SPEC[TC_P2_CANDS] = {{0, 192, 0}, {1, 48, 0}, {1, 192, 0}, {1, 192, 1}, {1, 768, 0}};
 
-// One phase-2 schedule of every network's upper-triangle P and C tiles.  A P
-// tile is one unit of the LPT assignment (its whole K) and is listed as its
-// K chunks, consecutively, on the pair it is assigned to (see P2Item).
+int p2_epi(long long mma_slots);
+
+// One phase-2 schedule of every network's upper-triangle P and C tiles (only
+// the networks whose phase-2 kernel configuration p2_epi is epi, if epi > 0).
+// A P tile is one unit of the LPT assignment (its whole K) and is listed as
+// its K chunks, consecutively, on the pair it is assigned to (see P2Item).
 void build_p2(const std::vector<const Dev *> &ds, int pairs, const P2Spec &sp, std::vector<int> &off,
-              std::vector<int> &tiles, std::vector<int> &nets)
+              std::vector<int> &tiles, std::vector<int> &nets, int epi = 0)
 {
     std::vector<std::pair<long long, std::pair<int, int>>> all;
     for (int k = 0; k < (int)ds.size(); ++k) {
         const Dev &d = *ds[k];
+        if (epi > 0 && p2_epi(tile_cost(d, false, 0)) != epi)
+            continue;
         for (int isP = 1; isP >= 0; --isP) {
             const int nb = ceil_div(isP ? d.Tp : d.Gp, N2);
             long long c = tile_cost(d, isP != 0, 0);
@@ -2242,7 +2247,6 @@ cudaError_t launch_iteration_tc(const Dev &d, int cur, cudaStream_t s, KernelEve
 // ---- sets of networks: one launch per phase over all networks' tiles ---------------
 struct TcSet {
     int n = 0, diag = 0, pairs = 0;
-    int epi2 = 12;            // epilogue warps of the phase-2 kernel (p2_epi over the largest C' tile)
     Dev *devs = nullptr;      // device copies of the networks' Dev
     TcMaps *maps = nullptr;   // their tensor maps
     int *parity = nullptr;
@@ -2255,8 +2259,15 @@ struct TcSet {
         int *off = nullptr;
     };
     struct P2 {               // a phase-2 schedule: per pair, a list of packed tiles and their networks
-        int pairs = 0;
-        int *off = nullptr, *tiles = nullptr, *nets = nullptr;
+        // one launch per phase-2 kernel configuration (p2_epi) among the networks, each network in
+        // the configuration of its own single runs: the configurations group a tile's row sums
+        // differently, so this keeps every network's results equal to its single run's
+        struct Part {
+            int epi2 = 12, pairs = 0;
+            int *off = nullptr, *tiles = nullptr, *nets = nullptr;
+        };
+        Part part[2];
+        int nparts = 0;
     };
     std::vector<P1> p1;
     std::vector<P2> p2;
@@ -2283,10 +2294,6 @@ cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out)
     TcSet *t = new TcSet;
     t->n = (int)ds.size();
     t->diag = ds[0]->diag;
-    long long slots = 0;
-    for (const Dev *d : ds)
-        slots = std::max<long long>(slots, tile_cost(*d, false, 0));
-    t->epi2 = p2_epi(slots);
     std::vector<Dev> hd;
     std::vector<TcMaps> hm;
     std::vector<int2> bl;
@@ -2323,13 +2330,22 @@ cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out)
                 e = upload(&c.off, off);
             t->p1.push_back(c);
         }
+        bool has[2] = {false, false};  // networks whose phase 2 runs 12 / 8 epilogue warps
+        for (const Dev *d : ds)
+            has[p2_epi(tile_cost(*d, false, 0)) == 8] = true;
         for (int q = 0; q < TC_P2_CANDS && !e; ++q) {
-            std::vector<int> off, tiles, nets;
-            build_p2(ds, t->pairs, TC_P2_SPEC[q], off, tiles, nets);
             TcSet::P2 c;
-            c.pairs = (int)off.size() - 1;
-            if (!(e = upload(&c.off, off)) && !(e = upload(&c.tiles, tiles)))
-                e = upload(&c.nets, nets);
+            for (int g = 0; g < 2 && !e; ++g) {
+                if (!has[g])
+                    continue;
+                std::vector<int> off, tiles, nets;
+                TcSet::P2::Part &pt = c.part[c.nparts++];
+                pt.epi2 = g ? 8 : 12;
+                build_p2(ds, t->pairs, TC_P2_SPEC[q], off, tiles, nets, pt.epi2);
+                pt.pairs = (int)off.size() - 1;
+                if (!(e = upload(&pt.off, off)) && !(e = upload(&pt.tiles, tiles)))
+                    e = upload(&pt.nets, nets);
+            }
             t->p2.push_back(c);
         }
     }
@@ -2351,7 +2367,7 @@ cudaError_t tc_set_launch(TcSet *t, int p1, int p2, cudaStream_t s, cudaEvent_t 
 {
     const TcSet::P1 &a1 = t->p1[p1];
     const TcSet::P2 &c = t->p2[p2];
-    SetArgs a{t->devs, t->maps, t->parity, a1.items, a1.off, t->acc, c.off, c.tiles, c.nets};
+    SetArgs a{t->devs, t->maps, t->parity, a1.items, a1.off, t->acc, nullptr, nullptr, nullptr};
     if (ev0)
         cudaEventRecord(ev0, s);
     k_tc_phase1_set<<<2 * t->pairs, THREADS1, phase1_smem(), s>>>(a);
@@ -2360,10 +2376,16 @@ cudaError_t tc_set_launch(TcSet *t, int p1, int p2, cudaStream_t s, cudaEvent_t 
         return e;
     if (ev1)
         cudaEventRecord(ev1, s);
-    if (t->epi2 == 8)
-        launch_p2_set<8>(t->diag == 2, 2 * c.pairs, s, a);
-    else
-        launch_p2_set<12>(t->diag == 2, 2 * c.pairs, s, a);
+    for (int g = 0; g < c.nparts; ++g) {
+        const TcSet::P2::Part &pt = c.part[g];
+        a.sched_off = pt.off;
+        a.sched = pt.tiles;
+        a.sched_net = pt.nets;
+        if (pt.epi2 == 8)
+            launch_p2_set<8>(t->diag == 2, 2 * pt.pairs, s, a);
+        else
+            launch_p2_set<12>(t->diag == 2, 2 * pt.pairs, s, a);
+    }
     if (ev2)
         cudaEventRecord(ev2, s);
     return launch_fin_tail_set(t->devs, t->blocks, t->nblocks, t->n, s);
@@ -2390,11 +2412,12 @@ void tc_set_destroy(TcSet *t)
         cudaFree(c.items);
         cudaFree(c.off);
     }
-    for (auto &c : t->p2) {
-        cudaFree(c.off);
-        cudaFree(c.tiles);
-        cudaFree(c.nets);
-    }
+    for (auto &c : t->p2)
+        for (auto &q : c.part) {
+            cudaFree(q.off);
+            cudaFree(q.tiles);
+            cudaFree(q.nets);
+        }
     delete t;
 }
 

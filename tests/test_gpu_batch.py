@@ -95,6 +95,30 @@ def test_batch_with_a_set_sized_network():
     print("\n250 x 15000 in a set, 2 iterations: " + ", ".join(f"{k} {v:.3e}" for k, v in e.items()))
 
 
+def test_batch_mixing_phase2_configurations():
+    """A network whose C' tiles are long enough for phase 2's eight-warp,
+    three-stage kernel (T = 1400 under BF16X3: 24 k-blocks, 288 MMA slots per
+    tile) in a set with small networks (twelve warps, two stages): the set
+    runs one phase-2 launch per configuration, each network in the one its
+    single run uses, so every network equals its single run bit for bit."""
+    from paper_1507_07039_gb300 import panda
+    wl = synth.custom(1400, 300, synth.BASE_SEED + 1401, n_samples=40, n_factors=4, p_density=0.01)
+    nets = [synth.make_inputs(wl)] + uneven_set(2, seed=13)
+    with panda.PandaBatch(nets, prec=1) as b:
+        _, iters, _ = b.run(0.1, 0.0, 3)
+        got = [b.get(k) for k in range(len(b))]
+    assert list(iters) == [3] * len(nets)
+    for k, (W0, P0, C0) in enumerate(nets):
+        single = gh.gpu_run(W0, P0, C0, 1, 0.1, 0.0, 3)
+        for a, g in zip((single["W"], single["P"], single["C"]), got[k]):
+            assert np.array_equal(a, g), f"network {k} differs from its single run"
+    orc = Oracle()
+    orc.set_threads(os.cpu_count() or 1)
+    W0, P0, C0 = nets[0]
+    o = gh.oracle_run(orc, W0, P0, C0, 0.1, 0.0, 3)
+    gh.assert_parity({"W": got[0][0], "P": got[0][1], "C": got[0][2]}, o, 1, "1400 x 300 in a mixed set")
+
+
 @pytest.mark.parametrize("prec", [1, 2, 3])
 def test_cut_tiles_give_the_bits_of_whole_tiles(prec):
     """1000 TFs x 5200 genes: 84 phase-1 tiles on 76 CTA pairs, so a context
