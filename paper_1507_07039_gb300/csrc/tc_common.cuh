@@ -429,24 +429,6 @@ __device__ __forceinline__ void drain(Sync<STAGES> &sy, Ctl *ctl)
         wait_bounded(&sy.full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u, &sy.abort, ctl, true);
 }
 
-// Sum v[q] over the 32 lanes so that lane l ends with the total for q = l
-// (31 shuffles; fixed order, so deterministic).
-__device__ __forceinline__ float lane_transpose_sum(float (&v)[32])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) {
-        const bool up = (lane & off) != 0;
-#pragma unroll
-        for (int k = 0; k < off; ++k) {
-            const float send = up ? v[k] : v[k + off];
-            const float keep = up ? v[k + off] : v[k];
-            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, off);
-        }
-    }
-    return v[0];
-}
-
 // Sum v[q] (16 values) over the 32 lanes so that lanes l and l ^ 16 both end
 // with the total for q = l & 15 (16 shuffles; fixed order, so deterministic).
 __device__ __forceinline__ float lane_transpose_sum16(float (&v)[16])
@@ -465,13 +447,7 @@ __device__ __forceinline__ float lane_transpose_sum16(float (&v)[16])
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-// named barriers among the epilogue warps only (128 or 256 threads)
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// named barrier among the 256 threads of eight epilogue warps
 __device__ __forceinline__ void epi_bar2() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
 
 }  // namespace tc
