@@ -413,7 +413,7 @@ int drive_begin(panda_ctx *c, float alpha, double tol, int max_iter, bool use_gr
         return set_err(c, PANDA_EINVAL, "iteration count would exceed the supported maximum (65536)");
     h.active = max_iter > 0;
     h.stop_at = ds.start + max_iter;
-    if (h.status && c->d.p1_flag)  // a run that gave up may have left a cut tile's flag raised
+    if (c->d.p1_flag)  // a run that gave up (a bounded wait ran out) may have left a cut tile's flag raised
         CU(cudaMemsetAsync(c->d.p1_flag, 0, (size_t)c->d.p1_cuts * 2 * sizeof(int), c->stream));
     h.status = 0;
     h.converged = 0;
