@@ -406,10 +406,10 @@ def run_reference(args, wl, rank, world):
 SEG = 100
 # Networks of a set with few TFs and many genes reach that limit first: after
 # 66-70 iterations for T ~ 240-300, G ~ 15000-17000 (measured over set64);
-# a set's warm-up (SET_WARM: the 22 schedule trials and one captured chunk)
+# a set's warm-up (SET_WARM: the 25 schedule trials and one captured chunk)
 # plus one segment stays within 60.
-SET_WARM = 30
-SEG_SET = 30
+SET_WARM = 34
+SEG_SET = 26
 
 
 def segments(n: int) -> list[int]:

@@ -1078,13 +1078,22 @@ __device__ __forceinline__ void epi_bar_p2()
     asm volatile("bar.sync 2, %0;" ::"n"(32 * EPI) : "memory");
 }
 
+// A tile row's sums for Eq. 6 are taken over four fixed column groups of
+// sub-chunks, [0, 5), [5, 8), [8, 10) and [10, 16), each added in column
+// order by one warp and then the four in group order: both epilogue
+// configurations (parts [0, 5), [5, 10), [10, 16) of twelve warps, [0, 8),
+// [8, 16) of eight) split along these boundaries, so the sums, and every
+// result, are the same to the bit whichever configuration runs.
+constexpr int P2_GROUPS = 4;
+__host__ __device__ constexpr int p2_group(int c) { return c < 5 ? 0 : c < 8 ? 1 : c < 10 ? 2 : 3; }
+
 template <bool SIM, int EPI>
 struct P2Cfg {
     static constexpr int THREADS = 64 + 32 * EPI;      // TMA warp, MMA warp, epilogue warps
     static constexpr int NS = SIM ? 3 : 2;             // sums per row: x, x^2 (and v^2 under D2)
     static constexpr int ST = EPI > 8 || SIM ? 2 : 3;  // pipeline stages that fit beside the epilogue buffers
     static constexpr size_t COLRED = 4 * NS * N2;      // [quarter][sum][column] floats
-    static constexpr size_t ROWRED = (EPI / 4) * NS * 128;  // [column part][sum][row] floats
+    static constexpr size_t ROWRED = P2_GROUPS * NS * 128;  // [column group][sum][row] floats
     static constexpr size_t COLNRM = N2;               // the tile's column norms
     static constexpr size_t BLK = 32 * 17;             // per epilogue warp: 32 x 16 staging block (padded)
 };
@@ -1424,6 +1433,16 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                               !*(volatile int *)&sy.abort;
             tc_fence_after();
             float r1 = 0.0f, r2 = 0.0f, rv = 0.0f;
+            // this warp's row sums of a column group, into its slot (zeros where nothing was summed)
+            auto flush = [&](int grp) {
+                rowred[(grp * NS + 0) * 128 + r] = r1;
+                rowred[(grp * NS + 1) * 128 + r] = r2;
+                if (SIM_SIGMA)
+                    rowred[(grp * NS + 2) * 128 + r] = rv;
+                r1 = r2 = rv = 0.0f;
+            };
+            for (int grp = p2_group(c_begin); grp <= p2_group(c_end - 1); ++grp)
+                flush(grp);  // (all zero: a timed-out tile leaves no stale sums)
             const uint32_t tbase = sy.tmem + buf * N2 + ((uint32_t)(wq * 32) << 16);
             // accumulator columns one sub-chunk ahead: each sub-chunk's TMEM load is issued once the
             // previous one's arithmetic is done and lands while that one's stores go out
@@ -1434,6 +1453,8 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
             for (int c = c_begin; c < c_end && live; ++c) {  // this warp's 16-column sub-chunks
                 const int cc = c * 16, j0 = n0 + cc;
                 const bool inside = krow && j0 < ld;
+                if (c > c_begin && p2_group(c) != p2_group(c - 1))
+                    flush(p2_group(c - 1));
                 float old[16], acc[16];
                 if (sst) {  // this lane's own row
 #pragma unroll
@@ -1672,10 +1693,8 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                 }
                 __syncwarp();  // the block is rewritten by the next sub-chunk
             }
-            rowred[(third * NS + 0) * 128 + r] = r1;
-            rowred[(third * NS + 1) * 128 + r] = r2;
-            if (SIM_SIGMA)
-                rowred[(third * NS + 2) * 128 + r] = rv;
+            if (live)
+                flush(p2_group(c_end - 1));
             epi_bar_p2<EPI>();
             if (live) {
 #pragma unroll
@@ -1692,8 +1711,8 @@ __device__ __forceinline__ void phase2_pair(const Src &src, Ctl *ctl)
                     if (tt < 128 && m0 + tt < ld) {
                         float rs = 0.0f;
 #pragma unroll
-                        for (int pp = 0; pp < PARTS; ++pp)
-                            rs += rowred[(pp * NS + wc) * 128 + tt];
+                        for (int grp = 0; grp < P2_GROUPS; ++grp)
+                            rs += rowred[(grp * NS + wc) * 128 + tt];
                         S[(size_t)bn * ld + m0 + tt] = rs;
                     }
                 }
@@ -1866,8 +1885,10 @@ constexpr long long BYTES_PER_SLOT = 7200;  // HBM bytes per pair in one BF16 MM
 // Phase-2 candidates: cost model, epilogue weight, order
 struct P2Spec {
     int roofline, epi, interleave;
+    int other;  // 1: the phase-2 kernel configuration p2_epi does not pick (12 warps / 2 stages <-> 8 / 3)
 };
-const P2Spec TC_P2_SPEC[TC_P2_CANDS] = {{0, 192, 0}, {1, 48, 0}, {1, 192, 0}, {1, 192, 1}, {1, 768, 0}};
+const P2Spec TC_P2_SPEC[TC_P2_CANDS] = {{0, 192, 0, 0}, {1, 48, 0, 0},  {1, 192, 0, 0},
+                                        {1, 192, 1, 0}, {1, 768, 0, 0}, {1, 192, 0, 1}};
 
 int p2_epi(long long mma_slots);
 
@@ -2091,10 +2112,12 @@ cudaError_t phase1_pairs(int &pairs, bool &all_resident, int *clusters_out = nul
 // Phase-1 candidates: the order of a network's tiles (LPT over persistent pairs by main-loop length)
 const char *const TC_P1_NAMES[TC_P1_CANDS] = {"tiles of a gene block together (C rows shared in L2)",
                                               "tiles of a TF block together (W rows shared in L2)"};
-// Phase-2 candidates (cost model, epilogue weight, order), as in TC_P2_SPEC
+// Phase-2 candidates (cost model, epilogue weight, order, kernel configuration), as in TC_P2_SPEC
 const char *const TC_P2_NAMES[TC_P2_CANDS] = {
     "LPT on MMA slots + 192", "LPT on max(MMA, HBM) + 48", "LPT on max(MMA, HBM) + 192",
-    "LPT on max(MMA, HBM) + 192, heavy and light tiles alternating", "LPT on max(MMA, HBM) + 768"};
+    "LPT on max(MMA, HBM) + 192, heavy and light tiles alternating", "LPT on max(MMA, HBM) + 768",
+    "LPT on max(MMA, HBM) + 192, the other phase-2 kernel configuration (8 epilogue warps and 3 stages "
+    "where the MMA-length model picks 12 and 2, or the reverse)"};
 
 int tc_phase1_plan(const Dev &d, int pairs, bool cut_ok, std::vector<int> &off, std::vector<int4> &items)
 {
@@ -2260,8 +2283,8 @@ struct TcSet {
     };
     struct P2 {               // a phase-2 schedule: per pair, a list of packed tiles and their networks
         // one launch per phase-2 kernel configuration (p2_epi) among the networks, each network in
-        // the configuration of its own single runs: the configurations group a tile's row sums
-        // differently, so this keeps every network's results equal to its single run's
+        // the configuration of its own single runs (the autotuner's last candidate swaps them; the
+        // two give the same bits: see p2_group)
         struct Part {
             int epi2 = 12, pairs = 0;
             int *off = nullptr, *tiles = nullptr, *nets = nullptr;
@@ -2340,8 +2363,9 @@ cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out)
                     continue;
                 std::vector<int> off, tiles, nets;
                 TcSet::P2::Part &pt = c.part[c.nparts++];
-                pt.epi2 = g ? 8 : 12;
-                build_p2(ds, t->pairs, TC_P2_SPEC[q], off, tiles, nets, pt.epi2);
+                // the networks whose single runs use configuration g; the candidate may run the other
+                build_p2(ds, t->pairs, TC_P2_SPEC[q], off, tiles, nets, g ? 8 : 12);
+                pt.epi2 = (g != 0) != (TC_P2_SPEC[q].other != 0) ? 8 : 12;
                 pt.pairs = (int)off.size() - 1;
                 if (!(e = upload(&pt.off, off)) && !(e = upload(&pt.tiles, tiles)))
                     e = upload(&pt.nets, nets);

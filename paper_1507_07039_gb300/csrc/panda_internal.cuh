@@ -254,7 +254,7 @@ struct TcSet;
 // Schedule candidates of the set engine's autotuner: phase 1 (the order of each
 // network's tiles in the persistent pairs' LPT lists) and phase 2 (cost model,
 // epilogue weight, order of the LPT lists); TC_*_NAMES describe them.
-constexpr int TC_P1_CANDS = 2, TC_P2_CANDS = 5;
+constexpr int TC_P1_CANDS = 2, TC_P2_CANDS = 6;
 extern const char *const TC_P1_NAMES[TC_P1_CANDS];
 extern const char *const TC_P2_NAMES[TC_P2_CANDS];
 cudaError_t tc_set_create(const std::vector<const Dev *> &ds, TcSet **out);

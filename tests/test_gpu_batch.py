@@ -66,7 +66,7 @@ def test_batch_runs_in_pieces(prec):
         for a, g in zip(ref[k], got[k]):
             assert np.array_equal(a, g), f"network {k} differs"
     # every candidate of both phases was timed (median of three) and the fastest is in use
-    assert sch["done"] and len(sch["p1_names"]) == 2 and len(sch["p2_names"]) == 5
+    assert sch["done"] and len(sch["p1_names"]) == 2 and len(sch["p2_names"]) == 6
     assert all(t > 0 for t in sch["p1_ms"]) and all(t > 0 for t in sch["p2_ms"])
     assert sch["p1"] == int(np.argmin(sch["p1_ms"])) and sch["p2"] == int(np.argmin(sch["p2_ms"]))
 
